@@ -1,0 +1,155 @@
+/*
+ * hg.h -- C ABI of the GB300-native HashGraph library (libhg.so).
+ *
+ * HashGraph (Green, "HashGraph - Scalable Hash Tables Using A Sparse Graph
+ * Data Structure", 2019) stores a static hash table as a CSR graph: bucket v
+ * (a "vertex", Section 3.1) owns the edges [offsets[v], offsets[v+1]) of the
+ * edge arrays (keys, ids).  The table always holds exactly n edges whatever
+ * the number of buckets V (Section 3.2, "HashGraph Collision Management").
+ *
+ * Conventions for every entry point
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *     never allocates, frees or retains them.  Host pointers (configs, table
+ *     views) are only read during the call.
+ *   - d_keys / d_ids / d_queries must be aligned to 16 bytes (tensors from a
+ *     CUDA caching allocator are); other device arrays to their element size.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  Argument errors are returned synchronously and launch
+ *     nothing.  A failed launch returns HG_ERR_CUDA.
+ *   - Calls that take a workspace write a device status word into it (bounded
+ *     waits that gave up, capacity overflow).  Read it after the stream has
+ *     finished with hg_workspace_status().
+ *   - Keys are uint32 or uint64.  Key value 0 and the maximum key are ordinary
+ *     keys: there is no empty-slot sentinel because there is no open
+ *     addressing (Section 3.2).
+ *   - Canonical table order: inside a bucket, edges appear in ascending input
+ *     position.  Every algorithm variant (V1, V2, any bin size, batched)
+ *     produces the same bytes.
+ */
+#ifndef HG_H
+#define HG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HG_OK = 0,
+  HG_ERR_INVALID_ARG = 1,         /* bad pointer, size, alignment or enum value */
+  HG_ERR_WORKSPACE_TOO_SMALL = 2, /* ws_bytes below the *_workspace_size() result */
+  HG_ERR_OVERFLOW = 3,            /* output capacity exceeded (device status) */
+  HG_ERR_CUDA = 4,                /* a CUDA launch or runtime call failed */
+  HG_ERR_TIMEOUT = 5,             /* a bounded device-side wait gave up (device status) */
+  HG_ERR_MODEL = 6,               /* malformed learned-map model blob */
+  HG_ERR_UNSUPPORTED = 7          /* valid request outside what this build supports */
+} hg_status;
+
+typedef enum { HG_KEY_U32 = 0, HG_KEY_U64 = 1 } hg_key_type;
+
+/* Bucket map.  MURMUR3: bucket = MurmurHash3_x86_32(key bytes, little-endian,
+ * 4 or 8 bytes, seed) mod V -- Eq. 1 of Section 2 ("hash(a) mod N/C_V").
+ * LEARNED: an order-preserving fp32 piecewise-linear CDF model (not in the
+ * paper; see hg_learned_train). */
+typedef enum { HG_MAP_MURMUR3 = 0, HG_MAP_LEARNED = 1 } hg_map_kind;
+
+/* Build algorithm.  V1 = Alg. 1 (one level: global histogram, prefix sum,
+ * scatter).  V2 = Alg. 2 (two levels: partition by hash range into bins, then
+ * build every bin in on-chip shared memory).  AUTO picks V2 when it applies. */
+typedef enum { HG_ALGO_AUTO = 0, HG_ALGO_V1 = 1, HG_ALGO_V2 = 2 } hg_algo;
+
+typedef struct {
+  int32_t key_type;          /* hg_key_type */
+  int32_t map;               /* hg_map_kind */
+  uint64_t num_buckets;      /* V = N / C_V (Eq. 1); 1 <= V <= 2^32 (V2: <= 2^30) */
+  uint32_t seed;             /* Murmur3 seed */
+  int32_t algo;              /* hg_algo */
+  const void* d_model;       /* learned map: device pointer to the model blob */
+  uint32_t bin_shift;        /* V2: log2(buckets per bin); 0 = automatic */
+  uint32_t threads_per_bin;  /* V2: threads of the bin-build kernel (512|1024); 0 = auto */
+} hg_config;
+
+/* A built table (read-only view).  offsets: uint32[V+1]; keys: n keys of
+ * cfg.key_type; ids: uint32[n] (the build input position, or the caller's id). */
+typedef struct {
+  uint64_t n;
+  const uint32_t* d_offsets;
+  const void* d_keys;
+  const uint32_t* d_ids;
+} hg_table;
+
+/* ---------------------------------------------------------------- build --
+ * HashGraph build (Alg. 1 / Alg. 2, Section 3.2-3.3).
+ *   d_keys     [n] keys (cfg->key_type)
+ *   d_ids      [n] uint32 ids, or NULL for ids = 0..n-1 (the input position,
+ *              "E[pos] <- (A[i], i)" in Alg. 1)
+ *   d_offsets  out [V+1] uint32: exclusive prefix sum of the bucket sizes,
+ *              offsets[0] = 0, offsets[V] = n
+ *   d_csr_keys out [n] keys grouped by bucket
+ *   d_csr_ids  out [n] ids in the same order
+ *   d_ws/ws_bytes  workspace of at least hg_build_workspace_size(cfg, n) bytes
+ * Requires n < 2^32.  Output buffers must not overlap the inputs. */
+size_t hg_build_workspace_size(const hg_config* cfg, uint64_t n);
+hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids, uint64_t n,
+                   uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, void* d_ws,
+                   size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- probe --
+ * HashGraph-Probe-Standard (Section 3.4): for each query, map it to its
+ * bucket and count every edge of that bucket whose key equals the query
+ * ("finds all instances", Section 5.2).
+ *   table      a table built with the same cfg (key type, V, map, seed)
+ *   d_queries  [q] keys;  d_counts out [q] uint32 match counts
+ * Needs no workspace. */
+hg_status hg_probe(const hg_config* cfg, const hg_table* table, const void* d_queries, uint64_t q,
+                   uint32_t* d_counts, void* stream);
+
+/* ----------------------------------------------------------------- join --
+ * HashGraph-Probe-New (Alg. 3, Section 3.4): both inputs are built into
+ * tables with the same V and map; bucket v of A is intersected with bucket v
+ * of B.  The inner-join size is the number of (a, b) edge pairs with equal
+ * keys.
+ * hg_join_count:
+ *   d_total          out [1] int64 join size
+ *   d_bucket_counts  out [V] int64 pairs per bucket, or NULL
+ * hg_join_materialize: writes every pair (A id, B id) in canonical order
+ * (bucket ascending, then A's CSR position, then B's CSR position).
+ *   d_build_ids, d_probe_ids  out [capacity] int64
+ *   d_total          out [1] int64 join size (also when it exceeds capacity;
+ *                    then only the first `capacity` pairs are written and the
+ *                    device status is HG_ERR_OVERFLOW)
+ * Both need hg_join_workspace_size(cfg, A->n, B->n) bytes of workspace. */
+size_t hg_join_workspace_size(const hg_config* cfg, uint64_t nA, uint64_t nB);
+hg_status hg_join_count(const hg_config* cfg, const hg_table* A, const hg_table* B,
+                        int64_t* d_total, int64_t* d_bucket_counts, void* d_ws, size_t ws_bytes,
+                        void* stream);
+hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_table* B,
+                              int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
+                              int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream);
+
+/* --------------------------------------------------------------- status --
+ * Device status word of a workspace (HG_OK when no device-side error was
+ * recorded).  Synchronises `stream` first.  hg_workspace_clear resets it. */
+hg_status hg_workspace_status(const void* d_ws, void* stream);
+hg_status hg_workspace_clear(void* d_ws, void* stream);
+const char* hg_status_string(hg_status s);
+const char* hg_version(void);
+
+/* ---------------------------------------------------------------- trace --
+ * Per-kernel timing.  While enabled, every kernel the library launches is
+ * bracketed by two CUDA events recorded on the launch stream.
+ * hg_profile_read synchronises on the recorded events and returns the number
+ * of distinct kernels; for the first max_entries of them it fills
+ * names[i] (static strings owned by the library), total_ms[i] (summed
+ * event-to-event time) and launches[i].  Any output pointer may be NULL.
+ * Returns -1 if an event query failed.  hg_profile_reset drops the records. */
+void hg_profile_enable(int on);
+void hg_profile_reset(void);
+int hg_profile_read(int max_entries, const char** names, double* total_ms, uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HG_H */

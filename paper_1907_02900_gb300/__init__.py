@@ -1,3 +1,293 @@
-"""GB300-native HashGraph (placeholder until the CUDA binding lands)."""
-def load():
-    raise RuntimeError("libhg.so not built yet")
+"""GB300-native HashGraph (Green, arXiv 1907.02900): Python binding of libhg.so.
+
+This module only marshals arguments: it allocates outputs and workspaces
+with PyTorch (device memory and streams are PyTorch's plumbing) and calls the
+C ABI declared in include/hg.h, where every step of the method runs as
+hand-written sm_103a CUDA.  There is no CPU fallback: if the CUDA library is
+missing or no GPU is present, calls raise.
+
+    import paper_1907_02900_gb300 as hg
+    t = hg.build(keys, num_buckets=1 << 20)          # keys: CUDA uint32/uint64 tensor
+    counts = hg.probe(t, queries)                    # per-query match counts
+    total, per_bucket = hg.join_count(tA, tB)        # Alg. 3 (same V and map)
+    a_ids, b_ids = hg.join_materialize(tA, tB)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBDIR = os.path.join(_HERE, "lib")
+LIBPATH = os.path.join(LIBDIR, "libhg.so")
+
+HG_OK = 0
+STATUS_NAMES = {0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_WORKSPACE_TOO_SMALL", 3: "HG_ERR_OVERFLOW",
+                4: "HG_ERR_CUDA", 5: "HG_ERR_TIMEOUT", 6: "HG_ERR_MODEL", 7: "HG_ERR_UNSUPPORTED"}
+KEY_U32, KEY_U64 = 0, 1
+MAP_MURMUR3, MAP_LEARNED = 0, 1
+ALGOS = {"auto": 0, "v1": 1, "v2": 2}
+
+
+class HGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class hg_config(ctypes.Structure):
+    _fields_ = [("key_type", ctypes.c_int32), ("map", ctypes.c_int32), ("num_buckets", ctypes.c_uint64),
+                ("seed", ctypes.c_uint32), ("algo", ctypes.c_int32), ("d_model", ctypes.c_void_p),
+                ("bin_shift", ctypes.c_uint32), ("threads_per_bin", ctypes.c_uint32)]
+
+
+class hg_table(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("d_offsets", ctypes.c_void_p), ("d_keys", ctypes.c_void_p),
+                ("d_ids", ctypes.c_void_p)]
+
+
+_lib = None
+
+# Entry points and their ctypes signatures; every name here is declared in include/hg.h.
+_VP, _SZ, _U64, _U32, _I32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int32
+_CFGP, _TABP = ctypes.POINTER(hg_config), ctypes.POINTER(hg_table)
+SIGNATURES = {
+    "hg_version": (ctypes.c_char_p, []),
+    "hg_status_string": (ctypes.c_char_p, [_I32]),
+    "hg_build_workspace_size": (_SZ, [_CFGP, _U64]),
+    "hg_build": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_probe": (_I32, [_CFGP, _TABP, _VP, _U64, _VP, _VP]),
+    "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
+    "hg_join_count": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_join_materialize": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
+    "hg_workspace_status": (_I32, [_VP, _VP]),
+    "hg_workspace_clear": (_I32, [_VP, _VP]),
+    "hg_profile_enable": (None, [ctypes.c_int]),
+    "hg_profile_reset": (None, []),
+    "hg_profile_read": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+}
+
+
+def profile_enable(on: bool = True):
+    load().hg_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().hg_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: (total ms, launches)} of the launches recorded while tracing was on."""
+    lib = load()
+    n = lib.hg_profile_read(0, None, None, None)
+    if n < 0:
+        raise HGError(4, "hg_profile_read")
+    names = (ctypes.c_char_p * max(n, 1))()
+    ms = (ctypes.c_double * max(n, 1))()
+    cnt = (ctypes.c_uint64 * max(n, 1))()
+    n = lib.hg_profile_read(n, names, ms, cnt)
+    return {names[i].decode(): (ms[i], int(cnt[i])) for i in range(n)}
+
+
+def build_library(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)["libhg.so"]
+
+
+def load(path: str | None = None):
+    """Load libhg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIBPATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1907_02900_gb300._build.build() "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != HG_OK:
+        raise HGError(code, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _key_type_of(t) -> int:
+    torch = _torch()
+    if t.dtype in (torch.uint32, torch.int32):
+        return KEY_U32
+    if t.dtype in (torch.uint64, torch.int64):
+        return KEY_U64
+    raise TypeError(f"keys must be 32- or 64-bit integers, got {t.dtype}")
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _require_cuda(t, name):
+    if t is not None and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t is not None and not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def make_config(key_type: int, num_buckets: int, seed: int = 0, algo: str = "auto", model=None,
+                bin_shift: int = 0) -> hg_config:
+    c = hg_config()
+    c.key_type = key_type
+    c.map = MAP_LEARNED if model is not None else MAP_MURMUR3
+    c.num_buckets = int(num_buckets)
+    c.seed = seed & 0xFFFFFFFF
+    c.algo = ALGOS[algo]
+    c.d_model = _ptr(model)
+    c.bin_shift = bin_shift
+    c.threads_per_bin = 0
+    return c
+
+
+@dataclass
+class Table:
+    """A built HashGraph: offsets[V+1], keys[n], ids[n] (CUDA tensors) and its config."""
+    offsets: object
+    keys: object
+    ids: object
+    cfg: hg_config
+    model: object = None
+
+    @property
+    def num_buckets(self) -> int:
+        return int(self.cfg.num_buckets)
+
+    def view(self) -> hg_table:
+        t = hg_table()
+        t.n = self.keys.numel()
+        t.d_offsets = self.offsets.data_ptr()
+        t.d_keys = self.keys.data_ptr()
+        t.d_ids = self.ids.data_ptr()
+        return t
+
+
+def build_workspace_size(cfg: hg_config, n: int) -> int:
+    return int(load().hg_build_workspace_size(ctypes.byref(cfg), n))
+
+
+def build_into(cfg: hg_config, keys, ids, offsets, csr_keys, csr_ids, ws, stream=None):
+    """hg_build on caller-provided tensors (no allocation)."""
+    lib = load()
+    rc = lib.hg_build(ctypes.byref(cfg), _ptr(keys), _ptr(ids), keys.numel(), _ptr(offsets), _ptr(csr_keys),
+                      _ptr(csr_ids), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_build")
+
+
+def build(keys, num_buckets: int, ids=None, seed: int = 0, algo: str = "auto", model=None,
+          bin_shift: int = 0, stream=None, ws=None) -> Table:
+    """HashGraph build (Alg. 1 V1 / Alg. 2 V2) of a CUDA key tensor."""
+    torch = _torch()
+    _require_cuda(keys, "keys")
+    _require_cuda(ids, "ids")
+    kt = _key_type_of(keys)
+    cfg = make_config(kt, num_buckets, seed, algo, model, bin_shift)
+    n = keys.numel()
+    dev = keys.device
+    need = build_workspace_size(cfg, n)
+    if need == 0:
+        raise HGError(1, "hg_build_workspace_size")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    offsets = torch.empty(num_buckets + 1, dtype=torch.uint32, device=dev)
+    csr_keys = torch.empty(n, dtype=keys.dtype, device=dev)
+    csr_ids = torch.empty(n, dtype=torch.uint32, device=dev)
+    build_into(cfg, keys, ids, offsets, csr_keys, csr_ids, ws, stream)
+    return Table(offsets, csr_keys, csr_ids, cfg, model)
+
+
+def probe_into(table: Table, queries, counts, stream=None):
+    lib = load()
+    tv = table.view()
+    rc = lib.hg_probe(ctypes.byref(table.cfg), ctypes.byref(tv), _ptr(queries), queries.numel(), _ptr(counts),
+                      _stream_handle(stream))
+    _check(rc, "hg_probe")
+
+
+def probe(table: Table, queries, stream=None):
+    """HashGraph-Probe-Standard: uint32 count of build keys equal to each query."""
+    torch = _torch()
+    _require_cuda(queries, "queries")
+    if _key_type_of(queries) != table.cfg.key_type:
+        raise TypeError("query key type differs from the table's")
+    counts = torch.empty(queries.numel(), dtype=torch.uint32, device=queries.device)
+    probe_into(table, queries, counts, stream)
+    return counts
+
+
+def join_workspace_size(cfg: hg_config, nA: int, nB: int) -> int:
+    return int(load().hg_join_workspace_size(ctypes.byref(cfg), nA, nB))
+
+
+def _same_space(A: Table, B: Table):
+    if A.cfg.num_buckets != B.cfg.num_buckets or A.cfg.key_type != B.cfg.key_type or A.cfg.map != B.cfg.map \
+            or A.cfg.seed != B.cfg.seed or A.model is not B.model:
+        raise ValueError("Alg. 3 needs both tables built with the same V and bucket map")
+
+
+def join_count(A: Table, B: Table, per_bucket: bool = True, stream=None, ws=None):
+    """Alg. 3 (HashGraph-Probe-New): inner-join size; optional int64 pairs per bucket."""
+    torch = _torch()
+    _same_space(A, B)
+    dev = A.keys.device
+    need = join_workspace_size(A.cfg, A.keys.numel(), B.keys.numel())
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    bc = torch.empty(A.num_buckets, dtype=torch.int64, device=dev) if per_bucket else None
+    ta, tb = A.view(), B.view()
+    rc = load().hg_join_count(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(total), _ptr(bc),
+                              _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_join_count")
+    return total, bc
+
+
+def join_materialize(A: Table, B: Table, capacity: int | None = None, stream=None, ws=None):
+    """Alg. 3 with the pairs written out: (A ids, B ids) int64 in canonical order."""
+    torch = _torch()
+    _same_space(A, B)
+    dev = A.keys.device
+    if capacity is None:
+        capacity = int(join_count(A, B, per_bucket=False, stream=stream)[0].item())
+    need = join_workspace_size(A.cfg, A.keys.numel(), B.keys.numel())
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    oa = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    ob = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    ta, tb = A.view(), B.view()
+    rc = load().hg_join_materialize(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(oa), _ptr(ob),
+                                    capacity, _ptr(total), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_join_materialize")
+    m = min(int(total.item()), capacity)
+    return oa[:m], ob[:m]
+
+
+def workspace_status(ws, stream=None) -> int:
+    return int(load().hg_workspace_status(_ptr(ws), _stream_handle(stream)))

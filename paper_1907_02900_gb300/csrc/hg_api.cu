@@ -1,0 +1,203 @@
+// C ABI entry points of libhg.so: argument checks, workspace layout and
+// dispatch to the kernels.  See include/hg.h for the contract.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "hg_build.cuh"
+#include "hg_probe.cuh"
+
+namespace hg {
+
+const DevInfo& dev_info() {
+  static DevInfo cache[64];
+  static bool init[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!init[dev]) {
+    cudaDeviceGetAttribute(&cache[dev].sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&cache[dev].max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (cache[dev].sms <= 0) cache[dev].sms = 152;
+    init[dev] = true;
+  }
+  return cache[dev];
+}
+
+hg_status last_launch_status() {
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HG_OK : HG_ERR_CUDA;
+}
+
+hg_status validate_config(const hg_config* cfg) {
+  if (!cfg) return HG_ERR_INVALID_ARG;
+  if (cfg->key_type != HG_KEY_U32 && cfg->key_type != HG_KEY_U64) return HG_ERR_INVALID_ARG;
+  if (cfg->map != HG_MAP_MURMUR3 && cfg->map != HG_MAP_LEARNED) return HG_ERR_INVALID_ARG;
+  if (cfg->num_buckets == 0 || cfg->num_buckets > (1ull << 32)) return HG_ERR_INVALID_ARG;
+  if (cfg->algo < HG_ALGO_AUTO || cfg->algo > HG_ALGO_V2) return HG_ERR_INVALID_ARG;
+  if (cfg->map == HG_MAP_LEARNED && !cfg->d_model) return HG_ERR_MODEL;
+  if (cfg->bin_shift > kMaxBinShift) return HG_ERR_INVALID_ARG;
+  if (cfg->threads_per_bin != 0 && cfg->threads_per_bin != 1024) return HG_ERR_UNSUPPORTED;
+  return HG_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// Which algorithm a build uses, and the V2 plan when it is V2.
+static hg_status choose_algo(const hg_config* cfg, uint64_t n, bool* use_v2, Plan* plan) {
+  const bool v2ok = make_plan_v2(cfg, n, plan);
+  if (cfg->algo == HG_ALGO_V2) {
+    if (!v2ok) return HG_ERR_UNSUPPORTED;
+    *use_v2 = true;
+  } else if (cfg->algo == HG_ALGO_V1) {
+    *use_v2 = false;
+  } else {
+    *use_v2 = v2ok;
+  }
+  return HG_OK;
+}
+
+}  // namespace hg
+
+using namespace hg;
+
+extern "C" {
+
+const char* hg_version(void) { return "hashgraph-gb300 0.1 (sm_103a)"; }
+
+const char* hg_status_string(hg_status s) {
+  switch (s) {
+    case HG_OK: return "ok";
+    case HG_ERR_INVALID_ARG: return "invalid argument";
+    case HG_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case HG_ERR_OVERFLOW: return "output capacity exceeded";
+    case HG_ERR_CUDA: return "CUDA error";
+    case HG_ERR_TIMEOUT: return "device-side wait timed out";
+    case HG_ERR_MODEL: return "invalid learned-map model";
+    case HG_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+size_t hg_build_workspace_size(const hg_config* cfg, uint64_t n) {
+  if (validate_config(cfg) != HG_OK) return 0;
+  bool v2 = false;
+  Plan p{};
+  if (choose_algo(cfg, n, &v2, &p) != HG_OK) return 0;
+  if (v2) return p.total;
+  return v1_workspace_bytes(cfg->key_type == HG_KEY_U64 ? 8 : 4, n, cfg->num_buckets);
+}
+
+hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids, uint64_t n,
+                   uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, void* d_ws,
+                   size_t ws_bytes, void* stream) {
+  hg_status rc = validate_config(cfg);
+  if (rc != HG_OK) return rc;
+  if (n >= (1ull << 32)) return HG_ERR_INVALID_ARG;
+  if (!d_offsets || !d_ws) return HG_ERR_INVALID_ARG;
+  if (n > 0 && (!d_keys || !d_csr_keys || !d_csr_ids)) return HG_ERR_INVALID_ARG;
+  if (!aligned(d_keys, 16) || !aligned(d_ids, 16) || !aligned(d_csr_keys, 16) || !aligned(d_csr_ids, 16) ||
+      !aligned(d_offsets, 4) || !aligned(d_ws, 256))
+    return HG_ERR_INVALID_ARG;
+  bool v2 = false;
+  Plan p{};
+  rc = choose_algo(cfg, n, &v2, &p);
+  if (rc != HG_OK) return rc;
+  const size_t need = v2 ? p.total : v1_workspace_bytes(cfg->key_type == HG_KEY_U64 ? 8 : 4, n, cfg->num_buckets);
+  if (ws_bytes < need) return HG_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+  if (n == 0) {
+    if (cudaMemsetAsync(d_offsets, 0, (size_t)(cfg->num_buckets + 1) * 4, st) != cudaSuccess) return HG_ERR_CUDA;
+    return HG_OK;
+  }
+  return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
+    using K = decltype(k);
+    if (v2)
+      return build_v2<K>(p, (const K*)d_keys, d_ids, d_offsets, (K*)d_csr_keys, d_csr_ids, (uint8_t*)d_ws, st, map);
+    return build_v1<K>(n, cfg->num_buckets, (const K*)d_keys, d_ids, d_offsets, (K*)d_csr_keys, d_csr_ids,
+                       (uint8_t*)d_ws, st, map);
+  });
+}
+
+hg_status hg_probe(const hg_config* cfg, const hg_table* table, const void* d_queries, uint64_t q,
+                   uint32_t* d_counts, void* stream) {
+  hg_status rc = validate_config(cfg);
+  if (rc != HG_OK) return rc;
+  if (!table || !table->d_offsets) return HG_ERR_INVALID_ARG;
+  if (q > 0 && (!d_queries || !d_counts)) return HG_ERR_INVALID_ARG;
+  if (table->n > 0 && !table->d_keys) return HG_ERR_INVALID_ARG;
+  const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  if (!aligned(d_queries, kb) || !aligned(table->d_keys, kb) || !aligned(d_counts, 4)) return HG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
+    using K = decltype(k);
+    return probe_launch<K>((const K*)d_queries, q, table->d_offsets, (const K*)table->d_keys, d_counts, st, map);
+  });
+}
+
+size_t hg_join_workspace_size(const hg_config* cfg, uint64_t nA, uint64_t nB) {
+  (void)nB;
+  if (validate_config(cfg) != HG_OK) return 0;
+  return join_workspace_bytes(nA, cfg->num_buckets);
+}
+
+static hg_status check_join_args(const hg_config* cfg, const hg_table* A, const hg_table* B, const void* d_ws) {
+  hg_status rc = validate_config(cfg);
+  if (rc != HG_OK) return rc;
+  if (!A || !B || !A->d_offsets || !B->d_offsets || !d_ws) return HG_ERR_INVALID_ARG;
+  if ((A->n > 0 && (!A->d_keys || !A->d_ids)) || (B->n > 0 && (!B->d_keys || !B->d_ids))) return HG_ERR_INVALID_ARG;
+  if (A->n >= (1ull << 32) || B->n >= (1ull << 32)) return HG_ERR_INVALID_ARG;
+  const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  if (!aligned(A->d_keys, kb) || !aligned(B->d_keys, kb) || !aligned(d_ws, 256)) return HG_ERR_INVALID_ARG;
+  return HG_OK;
+}
+
+hg_status hg_join_count(const hg_config* cfg, const hg_table* A, const hg_table* B, int64_t* d_total,
+                        int64_t* d_bucket_counts, void* d_ws, size_t ws_bytes, void* stream) {
+  hg_status rc = check_join_args(cfg, A, B, d_ws);
+  if (rc != HG_OK) return rc;
+  if (!d_total || !aligned(d_total, 8) || !aligned(d_bucket_counts, 8)) return HG_ERR_INVALID_ARG;
+  if (ws_bytes < join_workspace_bytes(A->n, cfg->num_buckets)) return HG_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+  return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
+    using K = decltype(k);
+    return join_count_impl<K>(cfg, A, B, d_total, d_bucket_counts, (uint8_t*)d_ws, st, map);
+  });
+}
+
+hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_table* B,
+                              int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
+                              int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream) {
+  hg_status rc = check_join_args(cfg, A, B, d_ws);
+  if (rc != HG_OK) return rc;
+  if (!d_total || !aligned(d_total, 8)) return HG_ERR_INVALID_ARG;
+  if (capacity > 0 && (!d_build_ids || !d_probe_ids)) return HG_ERR_INVALID_ARG;
+  if (!aligned(d_build_ids, 8) || !aligned(d_probe_ids, 8)) return HG_ERR_INVALID_ARG;
+  if (ws_bytes < join_workspace_bytes(A->n, cfg->num_buckets)) return HG_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+  return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
+    using K = decltype(k);
+    return join_materialize_impl<K>(cfg, A, B, d_build_ids, d_probe_ids, capacity, d_total, (uint8_t*)d_ws, st,
+                                    map);
+  });
+}
+
+hg_status hg_workspace_status(const void* d_ws, void* stream) {
+  if (!d_ws) return HG_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return HG_ERR_CUDA;
+  uint32_t s = 0;
+  if (cudaMemcpy(&s, d_ws, sizeof(s), cudaMemcpyDeviceToHost) != cudaSuccess) return HG_ERR_CUDA;
+  return (hg_status)s;
+}
+
+hg_status hg_workspace_clear(void* d_ws, void* stream) {
+  if (!d_ws) return HG_ERR_INVALID_ARG;
+  return cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), (cudaStream_t)stream) == cudaSuccess ? HG_OK : HG_ERR_CUDA;
+}
+
+}  // extern "C"

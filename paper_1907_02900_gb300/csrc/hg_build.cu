@@ -1,0 +1,885 @@
+// HashGraph build: V2 (Alg. 2, two-level, shared-memory bins) and V1 (Alg. 1).
+//
+// V2 on GB300 is organised as three streaming passes plus an on-chip finish:
+//   k_hist       per input chunk g: histogram of bins (bin = bucket >> s),
+//                bins held in shared memory (Alg. 2 Phase 1, "Bin Counting")
+//   k_colscan    per bin: exclusive prefix over chunks; bin totals
+//   k_scan_bins  exclusive scan of bin totals -> bin starts (Phase 2 prefix sum)
+//   k_partition  pass A: chunk -> super-bins (256-way stable partition);
+//                pass B: (super-bin, chunk) -> bins (<=256-way stable partition)
+//                (Phase 2, "Bin Placement and Data Reorganization")
+//   k_binbuild   per bin, in shared memory: local bucket index, stable counting
+//                sort, CSR offsets and edges (Phase 3, "HashGraph Creation")
+//   k_binbuild_big  bins larger than shared memory, streamed by one CTA each
+// Every partition is stable, so the table comes out in the canonical order
+// (bucket, then input position) without atomics deciding any position.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "hg_build.cuh"
+#include "hg_trace.h"
+#include "hg_partition.cuh"
+#include "hg_scan.cuh"
+
+namespace hg {
+
+// ===========================================================================
+// Plan
+// ===========================================================================
+static int ceil_log2_u64(uint64_t x) {
+  int l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+template <typename K>
+static constexpr int bin_ipt() {
+  return sizeof(K) == 4 ? 9 : 7;
+}
+
+size_t bin_smem_bytes(int kb, uint32_t emax) {
+  // two staging buffers of keys and ids, three u16 position arrays, u16 warp counters
+  size_t b = 2 * (size_t)(emax + 16) * (kb + 4) + 3 * (size_t)emax * 2 + 256 * kBinNW * 2;
+  return align_up(b, 16) + 32 * 4 + 2 * 8 + 64;
+}
+
+size_t big_smem_bytes(int kb, uint32_t nb) {
+  size_t b = (size_t)nb * 4 + (size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2 + 256 * kBinNW * 2;
+  return align_up(b, 16) + 32 * 4 + 64;
+}
+
+size_t part_smem_bytes(int kb, bool ids_in) {
+  size_t tile = kPartTile + 16;
+  size_t b = 2 * tile * kb + (ids_in ? 2 * tile * 4 : 0) + (size_t)kPartTile * (kb + 4 + 1) +
+             256 * kPartNW * 4 + 3 * 256 * 4;
+  return align_up(b, 16) + 32 * 4 + 2 * 8 + 64;
+}
+
+bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
+  const DevInfo& di = dev_info();
+  p->kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  p->n = n;
+  p->V = cfg->num_buckets;
+  p->emax = kBinNW * 32 * (p->kb == 4 ? bin_ipt<uint32_t>() : bin_ipt<uint64_t>());
+  const uint64_t V = p->V;
+  int s;
+  if (cfg->bin_shift) {
+    s = (int)cfg->bin_shift;
+  } else {
+    const double target = 0.75 * p->emax;
+    const double bpb = n ? target * (double)V / (double)n : (double)V;
+    s = bpb <= 1.0 ? 0 : (int)std::floor(std::log2(bpb));
+  }
+  s = std::max(s, ceil_log2_u64(V) - (int)kMaxBinsLog2);
+  s = std::max(s, 0);
+  if (s > (int)kMaxBinShift) return false;
+  p->s = (uint32_t)s;
+  const uint64_t nbins = ((V - 1) >> s) + 1;
+  if (nbins > (1ull << kMaxBinsLog2)) return false;
+  p->nbins = (uint32_t)nbins;
+  const int lb = ceil_log2_u64(nbins);
+  p->sshift = lb > 8 ? (uint32_t)(lb - 8) : 0u;
+  p->nsb = (uint32_t)(((nbins - 1) >> p->sshift) + 1);
+  const int sms = std::max(di.sms, 1);
+  uint64_t chunk = std::max<uint64_t>(kPartTile, (n + 2 * sms - 1) / (2 * sms));
+  chunk = (chunk + 15) / 16 * 16;
+  p->chunk = chunk;
+  p->G = (uint32_t)std::max<uint64_t>(1, (n + chunk - 1) / chunk);
+  size_t o = sizeof(WsHeader);
+  p->o_H = o;   o = align_up(o + (size_t)p->G * p->nbins * 4);
+  p->o_C = o;   o = align_up(o + (size_t)p->G * p->nsb * 4);
+  p->o_CT = o;  o = align_up(o + (size_t)p->nsb * 4);
+  p->o_T = o;   o = align_up(o + (size_t)p->nbins * 4);
+  p->o_BS = o;  o = align_up(o + ((size_t)p->nbins + 1) * 4);
+  p->o_ovf = o; o = align_up(o + (size_t)p->nbins * 4);
+  p->o_bk = o;  o = align_up(o + ((size_t)n + 16) * p->kb);
+  p->o_bi = o;  o = align_up(o + ((size_t)n + 16) * 4);
+  p->total = o;
+  return true;
+}
+
+// ===========================================================================
+// Kernels
+// ===========================================================================
+template <typename K>
+__device__ __forceinline__ void unpack16(const uint4& x, K (&k)[16 / sizeof(K)]);
+template <>
+__device__ __forceinline__ void unpack16<uint32_t>(const uint4& x, uint32_t (&k)[4]) {
+  k[0] = x.x; k[1] = x.y; k[2] = x.z; k[3] = x.w;
+}
+template <>
+__device__ __forceinline__ void unpack16<uint64_t>(const uint4& x, uint64_t (&k)[2]) {
+  k[0] = ((uint64_t)x.y << 32) | x.x;
+  k[1] = ((uint64_t)x.w << 32) | x.z;
+}
+
+// Phase 1: per-chunk bin histogram in shared memory; per super-bin sums.
+template <typename K, typename Map>
+__global__ void __launch_bounds__(kHistThreads) k_hist(const K* __restrict__ keys, uint64_t n,
+                                                       uint64_t chunk, uint32_t s, uint32_t nbins,
+                                                       uint32_t sshift, uint32_t nsb,
+                                                       uint32_t* __restrict__ H,
+                                                       uint32_t* __restrict__ C, Map map) {
+  extern __shared__ uint32_t hist[];
+  map.init();
+  for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  constexpr int per = 16 / sizeof(K);
+  const uint64_t c0 = (uint64_t)blockIdx.x * chunk;
+  const uint64_t c1 = min(c0 + chunk, n);
+  const uint64_t v0 = c0 / per, v1 = c1 / per;
+  const uint4* kv = reinterpret_cast<const uint4*>(keys);
+  const uint32_t bd = blockDim.x;
+  uint64_t v = v0 + threadIdx.x;
+  for (; v + 3 * (uint64_t)bd < v1; v += 4 * (uint64_t)bd) {
+    uint4 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = __ldcs(kv + v + u * bd);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      K k[per];
+      unpack16<K>(x[u], k);
+#pragma unroll
+      for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e]) >> s], 1u);
+    }
+  }
+  for (; v < v1; v += bd) {
+    K k[per];
+    unpack16<K>(__ldcs(kv + v), k);
+#pragma unroll
+    for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e]) >> s], 1u);
+  }
+  for (uint64_t i = max(v1 * per, c0) + threadIdx.x; i < c1; i += bd) atomicAdd(&hist[map(keys[i]) >> s], 1u);
+  __syncthreads();
+  uint32_t* row = H + (uint64_t)blockIdx.x * nbins;
+  for (uint32_t i = threadIdx.x; i < nbins; i += bd) row[i] = hist[i];
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5, nw = bd >> 5;
+  const uint32_t bps = 1u << sshift;
+  for (uint32_t sb = w; sb < nsb; sb += nw) {
+    uint32_t sum = 0;
+    for (uint32_t j = lane; j < bps; j += 32) {
+      const uint32_t b = (sb << sshift) + j;
+      if (b < nbins) sum += hist[b];
+    }
+    sum = warp_sum(sum);
+    if (lane == 0) C[(uint64_t)blockIdx.x * nsb + sb] = sum;
+  }
+}
+
+// Exclusive prefix down every column of a rows x cols table, in place;
+// column totals to coltot.
+__global__ void k_colscan(uint32_t* __restrict__ tab, uint32_t rows, uint32_t cols,
+                          uint32_t* __restrict__ coltot) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  uint32_t* p = tab + c;
+  uint32_t run = 0, g = 0;
+  for (; g + 8 <= rows; g += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = p[(uint64_t)(g + u) * cols];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      p[(uint64_t)(g + u) * cols] = run;
+      run += v[u];
+    }
+  }
+  for (; g < rows; ++g) {
+    const uint32_t v = p[(uint64_t)g * cols];
+    p[(uint64_t)g * cols] = run;
+    run += v;
+  }
+  if (coltot) coltot[c] = run;
+}
+
+// Exclusive scan of the bin totals (one CTA); list of bins too large for the
+// shared-memory bin build; closing CSR offset offsets[V] = n.
+__global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__ T, uint32_t nbins,
+                                                    uint32_t* __restrict__ BS, uint32_t emax,
+                                                    uint32_t* __restrict__ ovf_list,
+                                                    uint32_t* __restrict__ ovf_count,
+                                                    uint32_t* __restrict__ offsets, uint64_t V,
+                                                    uint32_t n) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
+  const uint32_t b = threadIdx.x * per, e = min(b + per, nbins);
+  uint32_t s = 0;
+  for (uint32_t i = b; i < e; ++i) s += T[i];
+  uint32_t total;
+  uint32_t base = block_excl_scan<uint32_t>(s, wsum, &total);
+  for (uint32_t i = b; i < e; ++i) {
+    BS[i] = base;
+    base += T[i];
+    if (T[i] > emax) ovf_list[atomicAdd(ovf_count, 1u)] = i;
+  }
+  if (threadIdx.x == 0) {
+    BS[nbins] = total;
+    offsets[V] = n;
+  }
+}
+
+// Phase 2 (both passes).  Pass A: items are input chunks; digit = super-bin.
+// Pass B: items are (super-bin, chunk) sub-ranges of pass A's output; digit =
+// bin inside the super-bin.  Tiles stream through shared memory by TMA bulk
+// copies, double-buffered; each tile is stably partitioned and written out
+// as contiguous runs.
+template <typename K>
+struct PartArgs {
+  const K* in_k;
+  const uint32_t* in_i;  // null: ids are input positions
+  K* out_k;
+  uint32_t* out_i;
+  uint64_t n, chunk;
+  uint32_t G, s, sshift, nbins, nsb;
+  const uint32_t* H;   // per (chunk, bin) exclusive column prefix
+  const uint32_t* C;   // per (chunk, super-bin) exclusive column prefix
+  const uint32_t* CT;  // per super-bin totals
+  const uint32_t* BS;  // bin starts
+  uint32_t* status;
+};
+
+template <typename K, typename Map, bool PASS_B>
+__global__ void __launch_bounds__(kPartNW * 32, 2) k_partition(PartArgs<K> a, Map map) {
+  constexpr int IPT = kPartIPT, NW = kPartNW;
+  constexpr uint32_t TILE = kPartTile;
+  constexpr uint32_t TB = TILE + 16;
+  const bool has_ids = PASS_B || a.in_i != nullptr;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sp = smem;
+  K* kin[2];
+  uint32_t* iin[2];
+  kin[0] = (K*)sp; sp += TB * sizeof(K);
+  kin[1] = (K*)sp; sp += TB * sizeof(K);
+  if (has_ids) {
+    iin[0] = (uint32_t*)sp; sp += TB * 4;
+    iin[1] = (uint32_t*)sp; sp += TB * 4;
+  } else {
+    iin[0] = iin[1] = nullptr;
+  }
+  K* sk = (K*)sp; sp += TILE * sizeof(K);
+  uint32_t* sv = (uint32_t*)sp; sp += TILE * 4;
+  uint32_t* wc = (uint32_t*)sp; sp += 256 * NW * 4;
+  uint32_t* dstart = (uint32_t*)sp; sp += 256 * 4;
+  uint32_t* cursor = (uint32_t*)sp; sp += 256 * 4;
+  uint32_t* scratch = (uint32_t*)sp; sp += 256 * 4;
+  uint8_t* sd = sp; sp += TILE;
+  sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
+  uint64_t* bar = (uint64_t*)sp;
+  (void)scratch;
+
+  map.init();
+  const uint64_t nitems = PASS_B ? (uint64_t)a.nsb * a.G : (uint64_t)a.G;
+  auto item_range = [&](uint64_t item, uint64_t& i0, uint64_t& i1) {
+    if (!PASS_B) {
+      i0 = item * a.chunk;
+      i1 = min(i0 + a.chunk, a.n);
+    } else {
+      const uint32_t sb = (uint32_t)(item / a.G), g = (uint32_t)(item % a.G);
+      const uint32_t c = a.C[(uint64_t)g * a.nsb + sb];
+      const uint32_t c_next = g + 1 < a.G ? a.C[(uint64_t)(g + 1) * a.nsb + sb] : a.CT[sb];
+      i0 = (uint64_t)a.BS[sb << a.sshift] + c;
+      i1 = i0 + (c_next - c);
+    }
+  };
+  // Tile stream of this CTA: items blockIdx.x, +gridDim.x, ...; tiles of TILE.
+  struct Ref {
+    uint64_t item, t0, t1;
+    bool ok;
+  };
+  auto first_from = [&](uint64_t item) -> Ref {
+    for (; item < nitems; item += gridDim.x) {
+      uint64_t i0, i1;
+      item_range(item, i0, i1);
+      if (i1 > i0) return Ref{item, i0, min(i0 + TILE, i1), true};
+    }
+    return Ref{0, 0, 0, false};
+  };
+  auto next_of = [&](const Ref& r) -> Ref {
+    uint64_t i0, i1;
+    item_range(r.item, i0, i1);
+    if (r.t1 < i1) return Ref{r.item, r.t1, min(r.t1 + TILE, i1), true};
+    return first_from(r.item + gridDim.x);
+  };
+  auto issue = [&](const Ref& r, int buf) {
+    if (threadIdx.x == 0) {
+      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(r.t0, r.t1);
+      uint32_t bytes = sk_.bytes();
+      TileSpan<4> si_{};
+      if (has_ids) {
+        si_ = tile_span<4>(r.t0, r.t1);
+        bytes += si_.bytes();
+      }
+      mbar_arrive_expect_tx(&bar[buf], bytes);
+      if (sk_.body) tma_load_1d(kin[buf], a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
+      if (has_ids && si_.body) tma_load_1d(iin[buf], a.in_i + si_.a0, si_.bytes(), &bar[buf]);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  Ref cur = first_from(blockIdx.x);
+  if (!cur.ok) return;
+  issue(cur, 0);
+  uint64_t cur_item = ~0ull;
+  int ndig = 0;
+  const uint32_t seg0 = (threadIdx.x >> 5) * (32u * IPT), lane = lane_id();
+  for (uint32_t it = 0; cur.ok; ++it) {
+    const int buf = it & 1;
+    const Ref nxt = next_of(cur);
+    if (nxt.ok) issue(nxt, buf ^ 1);
+    if (!mbar_wait_block(&bar[buf], (it >> 1) & 1u, a.status)) return;
+    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(cur.t0, cur.t1);
+    load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
+    TileSpan<4> si_{};
+    if (has_ids) {
+      si_ = tile_span<4>(cur.t0, cur.t1);
+      load_tail<4>(iin[buf], a.in_i, si_);
+    }
+    uint32_t sb = 0;
+    if (PASS_B) sb = (uint32_t)(cur.item / a.G);
+    if (cur.item != cur_item) {
+      cur_item = cur.item;
+      if (!PASS_B) {
+        ndig = (int)a.nsb;
+        for (int d = threadIdx.x; d < ndig; d += blockDim.x)
+          cursor[d] = a.BS[(uint32_t)d << a.sshift] + a.C[cur.item * a.nsb + d];
+      } else {
+        const uint32_t g = (uint32_t)(cur.item % a.G);
+        const uint32_t b0 = sb << a.sshift;
+        ndig = (int)min(1u << a.sshift, a.nbins - b0);
+        for (int d = threadIdx.x; d < ndig; d += blockDim.x)
+          cursor[d] = a.BS[b0 + d] + a.H[(uint64_t)g * a.nbins + b0 + d];
+      }
+    }
+    __syncthreads();
+    const uint32_t cnt = (uint32_t)(cur.t1 - cur.t0);
+    const K* kk = kin[buf] + (cur.t0 - sk_.a0);
+    const uint32_t* ii = has_ids ? iin[buf] + (cur.t0 - si_.a0) : nullptr;
+    K key[IPT];
+    uint32_t val[IPT], dig[IPT];
+#pragma unroll
+    for (int r = 0; r < IPT; ++r) {
+      const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+      if (idx < cnt) {
+        key[r] = kk[idx];
+        val[r] = has_ids ? ii[idx] : (uint32_t)(cur.t0 + idx);
+        const uint32_t bucket = map(key[r]);
+        dig[r] = PASS_B ? (bucket >> a.s) - (sb << a.sshift) : bucket >> (a.s + a.sshift);
+      } else {
+        key[r] = 0;
+        val[r] = 0;
+        dig[r] = 0;
+      }
+    }
+    tile_partition_out<K, IPT, NW>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                   a.out_k, a.out_i);
+    cur = nxt;
+  }
+}
+
+// Phase 3: build every bin in shared memory.  Persistent CTAs (one per SM)
+// take bins round-robin; the next bin's keys and ids are fetched by TMA
+// while the current one is sorted.  Bins above emax are skipped here.
+template <typename K>
+struct BinArgs {
+  const K* in_k;
+  const uint32_t* in_i;
+  K* csr_k;
+  uint32_t* csr_i;
+  uint32_t* offsets;
+  const uint32_t* T;
+  const uint32_t* BS;
+  uint64_t V;
+  uint32_t nbins, s, emax;
+  uint32_t* status;
+};
+
+template <typename K, typename Map, int IPT>
+__global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map map) {
+  constexpr int NW = kBinNW;
+  const uint32_t EB = a.emax + 16;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sp = smem;
+  K* kin[2];
+  uint32_t* iin[2];
+  kin[0] = (K*)sp; sp += (size_t)EB * sizeof(K);
+  kin[1] = (K*)sp; sp += (size_t)EB * sizeof(K);
+  iin[0] = (uint32_t*)sp; sp += (size_t)EB * 4;
+  iin[1] = (uint32_t*)sp; sp += (size_t)EB * 4;
+  uint16_t* lb = (uint16_t*)sp; sp += (size_t)a.emax * 2;
+  uint16_t* tmp = (uint16_t*)sp; sp += (size_t)a.emax * 2;
+  uint16_t* perm = (uint16_t*)sp; sp += (size_t)a.emax * 2;
+  uint16_t* wc = (uint16_t*)sp; sp += 256 * NW * 2;
+  sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
+  uint64_t* bar = (uint64_t*)sp;
+
+  map.init();
+  auto skip = [&](uint32_t b) {
+    while (b < a.nbins && a.T[b] > a.emax) b += gridDim.x;
+    return b;
+  };
+  auto issue = [&](uint32_t b, int buf) {
+    if (threadIdx.x == 0) {
+      const uint64_t k0 = a.BS[b], k1 = k0 + a.T[b];
+      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(k0, k1);
+      const TileSpan<4> si_ = tile_span<4>(k0, k1);
+      mbar_arrive_expect_tx(&bar[buf], sk_.bytes() + si_.bytes());
+      if (sk_.body) tma_load_1d(kin[buf], a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
+      if (si_.body) tma_load_1d(iin[buf], a.in_i + si_.a0, si_.bytes(), &bar[buf]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t b = skip(blockIdx.x);
+  if (b >= a.nbins) return;
+  issue(b, 0);
+  for (uint32_t it = 0; b < a.nbins; ++it) {
+    const int buf = it & 1;
+    const uint32_t nb_next = skip(b + gridDim.x);
+    if (nb_next < a.nbins) issue(nb_next, buf ^ 1);
+    if (!mbar_wait_block(&bar[buf], (it >> 1) & 1u, a.status)) return;
+    const uint32_t E = a.T[b], start = a.BS[b];
+    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(start, (uint64_t)start + E);
+    const TileSpan<4> si_ = tile_span<4>(start, (uint64_t)start + E);
+    load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
+    load_tail<4>(iin[buf], a.in_i, si_);
+    const uint64_t bucket0 = (uint64_t)b << a.s;
+    const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
+    __syncthreads();
+    const K* kk = kin[buf] + (start - sk_.a0);
+    const uint32_t* ii = iin[buf] + (start - si_.a0);
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
+      lb[e] = (uint16_t)(map(kk[e]) - (uint32_t)bucket0);
+    __syncthreads();
+    const uint16_t* sorted = sort_positions_by_bucket<IPT, NW, uint16_t>(lb, E, nb, tmp, perm, wc, wsum);
+    write_offsets_from_sorted(lb, sorted, E, nb, bucket0, start, a.offsets);
+    for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
+      const uint32_t p = sorted[j];
+      a.csr_k[start + j] = kk[p];
+      a.csr_i[start + j] = ii[p];
+    }
+    __syncthreads();
+    b = nb_next;
+  }
+}
+
+// Bins too large for shared memory (duplicates, skew, tiny V): one CTA per
+// bin.  Pass 1 counts local buckets into shared-memory cursors and writes the
+// bin's offsets; pass 2 streams the bin in tiles, sorts each tile stably by
+// local bucket and appends every run at its bucket cursor.
+template <typename K, typename Map>
+__global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, const uint32_t* ovf_list,
+                                                               const uint32_t* ovf_count, Map map) {
+  constexpr int NW = kBinNW, IPT = kBigTile / (NW * 32);
+  extern __shared__ __align__(16) uint8_t smem[];
+  map.init();
+  const uint32_t nbmax = 1u << a.s;
+  uint8_t* sp = smem;
+  uint32_t* cur = (uint32_t*)sp; sp += (size_t)nbmax * 4;
+  K* tk = (K*)sp; sp += (size_t)kBigTile * sizeof(K);
+  uint32_t* ti = (uint32_t*)sp; sp += (size_t)kBigTile * 4;
+  uint16_t* lb = (uint16_t*)sp; sp += kBigTile * 2;
+  uint16_t* tmp = (uint16_t*)sp; sp += kBigTile * 2;
+  uint16_t* perm = (uint16_t*)sp; sp += kBigTile * 2;
+  uint16_t* slb = (uint16_t*)sp; sp += kBigTile * 2;
+  uint16_t* wc = (uint16_t*)sp; sp += 256 * NW * 2;
+  sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  uint32_t* wsum = (uint32_t*)sp;
+  const uint32_t novf = *ovf_count;
+  for (uint32_t k = blockIdx.x; k < novf; k += gridDim.x) {
+    const uint32_t b = ovf_list[k];
+    const uint32_t E = a.T[b], start = a.BS[b];
+    const uint64_t bucket0 = (uint64_t)b << a.s;
+    const uint32_t nb = (uint32_t)min((uint64_t)nbmax, a.V - bucket0);
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) cur[v] = 0;
+    __syncthreads();
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
+      atomicAdd(&cur[map(a.in_k[start + e]) - (uint32_t)bucket0], 1u);
+    __syncthreads();
+    block_excl_scan_smem(cur, (int)nb, wsum);
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
+      a.offsets[bucket0 + v] = start + cur[v];
+      cur[v] += start;
+    }
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < E; t0 += kBigTile) {
+      const uint32_t cnt = min((uint32_t)kBigTile, E - t0);
+      for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const K key = a.in_k[start + t0 + e];
+        tk[e] = key;
+        ti[e] = a.in_i[start + t0 + e];
+        lb[e] = (uint16_t)(map(key) - (uint32_t)bucket0);
+      }
+      __syncthreads();
+      const uint16_t* sorted = sort_positions_by_bucket<IPT, NW, uint16_t>(lb, cnt, nb, tmp, perm, wc, wsum);
+      for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) slb[j] = lb[sorted[j]];
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const uint16_t l = slb[j];
+        uint32_t lo = 0, hi = j;  // first index with slb == l
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (slb[mid] < l) lo = mid + 1; else hi = mid;
+        }
+        const uint32_t g = cur[l] + (j - lo);
+        const uint32_t p = sorted[j];
+        a.csr_k[g] = tk[p];
+        a.csr_i[g] = ti[p];
+      }
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const uint16_t l = slb[j];
+        if (j + 1 == cnt || slb[j + 1] != l) {
+          uint32_t lo = 0, hi = j;
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (slb[mid] < l) lo = mid + 1; else hi = mid;
+          }
+          cur[l] += j - lo + 1;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ===========================================================================
+// V1 (Alg. 1): global histogram with atomics, prefix sum, atomic scatter.
+// Atomics leave the order inside a bucket arbitrary; a fix-up then sorts
+// every bucket by input position (the ids hold positions until the end).
+// ===========================================================================
+template <typename K, typename Map>
+__global__ void k_v1_count(const K* __restrict__ keys, uint64_t n, uint32_t* __restrict__ counts, Map map) {
+  map.init();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    atomicAdd(&counts[map(keys[i])], 1u);
+}
+
+template <typename K, typename Map>
+__global__ void k_v1_scatter(const K* __restrict__ keys, uint64_t n, const uint32_t* __restrict__ offsets,
+                             uint32_t* __restrict__ cursor, K* __restrict__ csr_k,
+                             uint32_t* __restrict__ csr_i, Map map) {
+  map.init();
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const K key = keys[i];
+    const uint32_t b = map(key);
+    const uint32_t pos = offsets[b] + atomicAdd(&cursor[b], 1u);
+    csr_k[pos] = key;
+    csr_i[pos] = (uint32_t)i;
+  }
+}
+
+// Buckets of up to kV1Small edges: insertion sort by position, one thread per
+// bucket.  Longer buckets go to a list for k_v1_fix_heavy.
+template <typename K>
+__global__ void k_v1_fix_small(const uint32_t* __restrict__ offsets, uint64_t V, K* csr_k, uint32_t* csr_i,
+                               uint32_t* heavy_list, uint32_t* heavy_count) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = offsets[v], e = offsets[v + 1];
+    const uint32_t c = e - s;
+    if (c <= 1) continue;
+    if (c > kV1Small) {
+      heavy_list[atomicAdd(heavy_count, 1u)] = (uint32_t)v;
+      continue;
+    }
+    for (uint32_t i = s + 1; i < e; ++i) {
+      const uint32_t p = csr_i[i];
+      const K k = csr_k[i];
+      uint32_t j = i;
+      while (j > s && csr_i[j - 1] > p) {
+        csr_i[j] = csr_i[j - 1];
+        csr_k[j] = csr_k[j - 1];
+        --j;
+      }
+      csr_i[j] = p;
+      csr_k[j] = k;
+    }
+  }
+}
+
+// Heavy buckets: one CTA per bucket, least-significant-digit radix sort of
+// the (position, key) pairs by position, 8 bits per pass.  Segments that fit
+// shared memory are sorted in place there; longer ones stream through a
+// global temporary, one stable tile partition at a time.
+template <typename K>
+__global__ void __launch_bounds__(kV1HeavyNW * 32) k_v1_fix_heavy(const uint32_t* __restrict__ offsets,
+                                                                 const uint32_t* heavy_list,
+                                                                 const uint32_t* heavy_count, K* csr_k,
+                                                                 uint32_t* csr_i, K* tmp_k, uint32_t* tmp_i,
+                                                                 uint32_t nbits) {
+  constexpr int NW = kV1HeavyNW, IPT = kPartIPT;
+  constexpr uint32_t TILE = NW * 32 * IPT;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint8_t* sp = smem;
+  K* sk = (K*)sp; sp += TILE * sizeof(K);
+  uint32_t* sv = (uint32_t*)sp; sp += TILE * 4;
+  uint32_t* wc = (uint32_t*)sp; sp += 256 * NW * 4;
+  uint32_t* dstart = (uint32_t*)sp; sp += 256 * 4;
+  uint32_t* cursor = (uint32_t*)sp; sp += 256 * 4;
+  uint8_t* sd = sp; sp += TILE;
+  sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  uint32_t* wsum = (uint32_t*)sp;
+  const uint32_t seg0 = (threadIdx.x >> 5) * (32u * IPT), lane = lane_id();
+  const uint32_t nh = *heavy_count;
+  for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const uint32_t v = heavy_list[h];
+    const uint32_t s = offsets[v], c = offsets[v + 1] - s;
+    K* src_k = csr_k + s;
+    uint32_t* src_i = csr_i + s;
+    K* dst_k = tmp_k + s;
+    uint32_t* dst_i = tmp_i + s;
+    for (uint32_t shift = 0; shift < nbits; shift += 8) {
+      // count digits of this pass
+      for (int d = threadIdx.x; d < 256; d += blockDim.x) cursor[d] = 0;
+      __syncthreads();
+      for (uint32_t e = threadIdx.x; e < c; e += blockDim.x) atomicAdd(&cursor[(src_i[e] >> shift) & 255u], 1u);
+      __syncthreads();
+      block_excl_scan_smem(cursor, 256, wsum);
+      for (uint32_t t0 = 0; t0 < c; t0 += TILE) {
+        const uint32_t cnt = min(TILE, c - t0);
+        K key[IPT];
+        uint32_t val[IPT], dig[IPT];
+#pragma unroll
+        for (int r = 0; r < IPT; ++r) {
+          const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+          if (idx < cnt) {
+            key[r] = src_k[t0 + idx];
+            val[r] = src_i[t0 + idx];
+            dig[r] = (val[r] >> shift) & 255u;
+          } else {
+            key[r] = 0; val[r] = 0; dig[r] = 0;
+          }
+        }
+        tile_partition_out<K, IPT, NW>(key, val, dig, cnt, 256, sk, sv, sd, wc, dstart, cursor, wsum,
+                                       dst_k, dst_i);
+      }
+      K* tk = src_k; src_k = dst_k; dst_k = tk;
+      uint32_t* tv = src_i; src_i = dst_i; dst_i = tv;
+    }
+    if (src_k != csr_k + s) {  // odd number of passes: copy back
+      for (uint32_t e = threadIdx.x; e < c; e += blockDim.x) {
+        csr_k[s + e] = src_k[e];
+        csr_i[s + e] = src_i[e];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_v1_ids(uint32_t* __restrict__ csr_i, const uint32_t* __restrict__ ids, uint64_t n) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x)
+    csr_i[j] = ids[csr_i[j]];
+}
+
+// ===========================================================================
+// Host drivers
+// ===========================================================================
+template <typename F>
+static void set_smem_once(F* kernel, size_t bytes) {
+  // The attribute is per kernel; setting it every call is cheap and idempotent.
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename K, typename Map>
+hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map) {
+  WsHeader* hdr = (WsHeader*)ws;
+  uint32_t* status = &hdr->status;
+  uint32_t* H = (uint32_t*)(ws + p.o_H);
+  uint32_t* C = (uint32_t*)(ws + p.o_C);
+  uint32_t* CT = (uint32_t*)(ws + p.o_CT);
+  uint32_t* T = (uint32_t*)(ws + p.o_T);
+  uint32_t* BS = (uint32_t*)(ws + p.o_BS);
+  uint32_t* ovf = (uint32_t*)(ws + p.o_ovf);
+  K* bk = (K*)(ws + p.o_bk);
+  uint32_t* bi = (uint32_t*)(ws + p.o_bi);
+  const DevInfo& di = dev_info();
+
+  {
+    const size_t sm = (size_t)p.nbins * 4;
+    auto kern = k_hist<K, Map>;
+    set_smem_once(kern, sm);
+    {
+      HG_TRACE("k_hist", st);
+      kern<<<p.G, kHistThreads, sm, st>>>(keys, p.n, p.chunk, p.s, p.nbins, p.sshift, p.nsb, H, C, map);
+    }
+  }
+  {
+    HG_TRACE("k_colscan", st);
+    k_colscan<<<(p.nbins + 255) / 256, 256, 0, st>>>(H, p.G, p.nbins, T);
+  }
+  {
+    HG_TRACE("k_colscan", st);
+    k_colscan<<<(p.nsb + 255) / 256, 256, 0, st>>>(C, p.G, p.nsb, CT);
+  }
+  {
+    HG_TRACE("k_scan_bins", st);
+    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, p.emax, ovf, &hdr->ovf_count, offsets, p.V, (uint32_t)p.n);
+  }
+
+  const bool two = p.sshift > 0;
+  PartArgs<K> pa{};
+  pa.in_k = keys;
+  pa.in_i = ids;
+  pa.out_k = csr_k;  // pass A output lives in the caller's CSR arrays until pass B
+  pa.out_i = csr_i;
+  pa.n = p.n;
+  pa.chunk = p.chunk;
+  pa.G = p.G;
+  pa.s = p.s;
+  pa.sshift = p.sshift;
+  pa.nbins = p.nbins;
+  pa.nsb = p.nsb;
+  pa.H = H;
+  pa.C = C;
+  pa.CT = CT;
+  pa.BS = BS;
+  pa.status = status;
+  {
+    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr);
+    auto kern = k_partition<K, Map, false>;
+    set_smem_once(kern, sm);
+    {
+      HG_TRACE("k_partition_A", st);
+      kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
+    }
+  }
+  if (two) {
+    PartArgs<K> pb = pa;
+    pb.in_k = csr_k;
+    pb.in_i = csr_i;
+    pb.out_k = bk;
+    pb.out_i = bi;
+    const size_t sm = part_smem_bytes(sizeof(K), true);
+    auto kern = k_partition<K, Map, true>;
+    set_smem_once(kern, sm);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPartNW * 32, sm);
+    const uint64_t items = (uint64_t)p.nsb * p.G;
+    const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)std::max(1, per_sm) * di.sms);
+    {
+      HG_TRACE("k_partition_B", st);
+      kern<<<grid, kPartNW * 32, sm, st>>>(pb, map);
+    }
+  }
+  BinArgs<K> ba{};
+  ba.in_k = two ? bk : csr_k;
+  ba.in_i = two ? bi : csr_i;
+  ba.csr_k = csr_k;
+  ba.csr_i = csr_i;
+  ba.offsets = offsets;
+  ba.T = T;
+  ba.BS = BS;
+  ba.V = p.V;
+  ba.nbins = p.nbins;
+  ba.s = p.s;
+  ba.emax = p.emax;
+  ba.status = status;
+  {
+    constexpr int IPT = bin_ipt<K>();
+    const size_t sm = bin_smem_bytes(sizeof(K), p.emax);
+    auto kern = k_binbuild<K, Map, IPT>;
+    set_smem_once(kern, sm);
+    const unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms);
+    {
+      HG_TRACE("k_binbuild", st);
+      kern<<<grid, kBinNW * 32, sm, st>>>(ba, map);
+    }
+  }
+  {
+    const size_t sm = big_smem_bytes(sizeof(K), 1u << p.s);
+    auto kern = k_binbuild_big<K, Map>;
+    set_smem_once(kern, sm);
+    const unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms);
+    {
+      HG_TRACE("k_binbuild_big", st);
+      kern<<<grid, kBinNW * 32, sm, st>>>(ba, ovf, &hdr->ovf_count, map);
+    }
+  }
+  return last_launch_status();
+}
+
+size_t v1_workspace_bytes(int kb, uint64_t n, uint64_t V) {
+  size_t o = sizeof(WsHeader);
+  o = align_up(o + (size_t)V * 4);                  // cursors
+  o = align_up(o + scan_workspace_bytes<uint32_t>(V + 1));    // scan partials
+  o = align_up(o + (size_t)V * 4);                  // heavy list
+  o = align_up(o + ((size_t)n + 16) * kb);          // temp keys
+  o = align_up(o + ((size_t)n + 16) * 4);           // temp positions
+  return o;
+}
+
+template <typename K, typename Map>
+hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map) {
+  WsHeader* hdr = (WsHeader*)ws;
+  size_t o = sizeof(WsHeader);
+  uint32_t* cursor = (uint32_t*)(ws + o); o = align_up(o + (size_t)V * 4);
+  uint32_t* part = (uint32_t*)(ws + o);   o = align_up(o + scan_workspace_bytes<uint32_t>(V + 1));
+  uint32_t* heavy = (uint32_t*)(ws + o);  o = align_up(o + (size_t)V * 4);
+  K* tk = (K*)(ws + o);                   o = align_up(o + ((size_t)n + 16) * sizeof(K));
+  uint32_t* ti = (uint32_t*)(ws + o);
+  const int sms = dev_info().sms;
+  const unsigned grid = (unsigned)std::max(1, sms * 8);
+  cudaMemsetAsync(offsets, 0, (size_t)(V + 1) * 4, st);
+  cudaMemsetAsync(cursor, 0, (size_t)V * 4, st);
+  {
+    HG_TRACE("k_v1_count", st);
+    k_v1_count<K, Map><<<grid, 256, 0, st>>>(keys, n, offsets, map);
+  }
+  hg_status rc = device_excl_scan<uint32_t>(offsets, V + 1, part, st);
+  if (rc != HG_OK) return rc;
+  {
+    HG_TRACE("k_v1_scatter", st);
+    k_v1_scatter<K, Map><<<grid, 256, 0, st>>>(keys, n, offsets, cursor, csr_k, csr_i, map);
+  }
+  {
+    HG_TRACE("k_v1_fix_small", st);
+    k_v1_fix_small<K><<<grid, 256, 0, st>>>(offsets, V, csr_k, csr_i, heavy, &hdr->heavy_count);
+  }
+  uint32_t nbits = 8;
+  while (nbits < 32 && (n - 1) >> nbits) nbits += 8;
+  {
+    const size_t sm = align_up((size_t)kV1HeavyNW * 32 * kPartIPT * (sizeof(K) + 5) + 256 * kV1HeavyNW * 4 +
+                               2 * 256 * 4, 16) + 32 * 4 + 64;
+    auto kern = k_v1_fix_heavy<K>;
+    set_smem_once(kern, sm);
+    {
+      HG_TRACE("k_v1_fix_heavy", st);
+      kern<<<(unsigned)std::max(1, sms), kV1HeavyNW * 32, sm, st>>>(offsets, heavy, &hdr->heavy_count, csr_k,
+                                                                    csr_i, tk, ti, nbits);
+    }
+  }
+  if (ids) {
+    HG_TRACE("k_v1_ids", st);
+    k_v1_ids<<<grid, 256, 0, st>>>(csr_i, ids, n);
+  }
+  return last_launch_status();
+}
+
+// Explicit instantiations used by hg_api.cu (build entry point).
+#define HG_INST(K, M)                                                                                   \
+  template hg_status build_v2<K, M>(const Plan&, const K*, const uint32_t*, uint32_t*, K*, uint32_t*, \
+                                    uint8_t*, cudaStream_t, M);                                         \
+  template hg_status build_v1<K, M>(uint64_t, uint64_t, const K*, const uint32_t*, uint32_t*, K*,       \
+                                    uint32_t*, uint8_t*, cudaStream_t, M);
+HG_INST(uint32_t, MurmurMap)
+HG_INST(uint64_t, MurmurMap)
+HG_INST(uint32_t, LearnedMap)
+HG_INST(uint64_t, LearnedMap)
+#undef HG_INST
+
+}  // namespace hg

@@ -1,0 +1,87 @@
+// Declarations shared between the build translation unit and the API layer.
+#pragma once
+
+#include "hg_device.cuh"
+
+namespace hg {
+
+constexpr int kHistThreads = 1024;
+constexpr uint32_t kMaxBinsLog2 = 15;  // bins counted in one shared-memory histogram
+constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local index, 128 KB cursors)
+constexpr int kPartNW = 16;            // warps of the partition kernels
+constexpr int kPartIPT = 8;            // items per thread
+constexpr int kPartTile = kPartNW * 32 * kPartIPT;  // 4096 elements per tile
+constexpr int kBinNW = 32;             // warps of the bin-build kernels (1024 threads)
+constexpr int kBigTile = 4096;         // tile of the oversized-bin kernel
+constexpr uint32_t kV1Small = 32;      // V1 fix-up: longest bucket sorted by one thread
+constexpr int kV1HeavyNW = 16;
+
+// V2 launch plan and workspace layout.
+struct Plan {
+  int kb;            // key bytes
+  uint64_t n, V;
+  uint32_t s;        // log2(buckets per bin)
+  uint32_t sshift;   // log2(bins per super-bin)
+  uint32_t nbins, nsb;
+  uint32_t G;        // input chunks of pass A
+  uint64_t chunk;    // elements per chunk (multiple of 16)
+  uint32_t emax;     // largest bin built in shared memory
+  size_t o_H, o_C, o_CT, o_T, o_BS, o_ovf, o_bk, o_bi, total;
+};
+
+bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p);
+size_t v1_workspace_bytes(int kb, uint64_t n, uint64_t V);
+
+template <typename K, typename Map>
+hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map);
+template <typename K, typename Map>
+hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, uint32_t* offsets,
+                   K* csr_k, uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map);
+
+// Bucket-map construction on the host.
+inline MurmurMap make_murmur(uint32_t seed, uint64_t V) {
+  MurmurMap m{};
+  m.seed = seed;
+  m.mod.d = V;
+  if ((V & (V - 1)) == 0) {
+    m.mod.pow2 = 1;
+    m.mod.mask = (uint32_t)(V - 1);
+    m.mod.M = 0;
+  } else {
+    m.mod.pow2 = 0;
+    m.mod.mask = 0;
+    m.mod.M = ~0ull / V + 1;
+  }
+  return m;
+}
+inline LearnedMap make_learned(const void* blob, uint64_t V) {
+  LearnedMap m{};
+  m.blob = (const uint8_t*)blob;
+  m.Vcap = V;
+  return m;
+}
+
+// Calls f(K{}, map) with the key type and map the config names.
+template <typename F>
+hg_status dispatch_key_map(const hg_config* cfg, F&& f) {
+  if (cfg->map == HG_MAP_LEARNED) {
+    LearnedMap m = make_learned(cfg->d_model, cfg->num_buckets);
+    return cfg->key_type == HG_KEY_U64 ? f(uint64_t{}, m) : f(uint32_t{}, m);
+  }
+  MurmurMap m = make_murmur(cfg->seed, cfg->num_buckets);
+  return cfg->key_type == HG_KEY_U64 ? f(uint64_t{}, m) : f(uint32_t{}, m);
+}
+
+}  // namespace hg
+
+namespace hg {
+size_t join_workspace_bytes(uint64_t nA, uint64_t V);
+template <typename K, typename Map>
+hg_status join_count_impl(const hg_config* cfg, const hg_table* A, const hg_table* B, int64_t* d_total,
+                          int64_t* d_bucket_counts, uint8_t* ws, cudaStream_t st, Map map);
+template <typename K, typename Map>
+hg_status join_materialize_impl(const hg_config* cfg, const hg_table* A, const hg_table* B, int64_t* outA,
+                                int64_t* outB, uint64_t cap, int64_t* d_total, uint8_t* ws, cudaStream_t st,
+                                Map map);
+}  // namespace hg

@@ -1,0 +1,382 @@
+// Device-side building blocks of the GB300 HashGraph library.
+//
+// Everything here is sm_103a device code: the Murmur3 bucket map (Eq. 1),
+// the learned bucket map, warp/block scans, the stable block-wide ranking
+// used by every partition step, and bounded TMA bulk-copy waits.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hg_internal.h"
+
+namespace hg {
+
+constexpr int kWarp = 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// MurmurHash3 x86_32 over the 4 or 8 little-endian bytes of a key (the hash
+// the paper names in Section 2, "Hashing").  Keys are whole 4-byte blocks,
+// so there is never a tail.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t mm3_mix_block(uint32_t h, uint32_t k) {
+  k *= 0xcc9e2d51u;
+  k = __funnelshift_l(k, k, 15);
+  k *= 0x1b873593u;
+  h ^= k;
+  h = __funnelshift_l(h, h, 13);
+  return h * 5u + 0xe6546b64u;
+}
+__device__ __forceinline__ uint32_t mm3_finish(uint32_t h, uint32_t len) {
+  h ^= len;
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint32_t murmur3(uint32_t key, uint32_t seed) {
+  return mm3_finish(mm3_mix_block(seed, key), 4u);
+}
+__device__ __forceinline__ uint32_t murmur3(uint64_t key, uint32_t seed) {
+  uint32_t h = mm3_mix_block(seed, (uint32_t)key);
+  h = mm3_mix_block(h, (uint32_t)(key >> 32));
+  return mm3_finish(h, 8u);
+}
+
+// h mod d for 32-bit h without a divide: Lemire, Kaser and Kurz, "Faster
+// remainder by direct computation" (2019).  M = floor((2^64-1)/d) + 1; then
+// h mod d = high64((M*h mod 2^64) * d).  Powers of two use a mask.
+struct FastMod {
+  uint64_t M;
+  uint64_t d;
+  uint32_t mask;
+  uint32_t pow2;
+  __device__ __forceinline__ uint32_t operator()(uint32_t h) const {
+    if (pow2) return h & mask;
+    return (uint32_t)__umul64hi(M * (uint64_t)h, d);
+  }
+};
+
+// Eq. 1: bucket = hash(key) mod V.
+struct MurmurMap {
+  uint32_t seed;
+  FastMod mod;
+  __device__ __forceinline__ void init() {}
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K key) const {
+    return mod(murmur3(key, seed));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Learned bucket map (not in the paper).  Two-layer piecewise-linear CDF
+// model stored as a blob in device memory:
+//   header 32 B: u32 magic, u32 L, u64 V, f32 root_a, f32 root_b, u32 key_type, u32 flags
+//   leaf   24 B: u64 xmin, f32 slope, f32 icpt, u32 base, u32 width
+// Root: leaf = clamp(floor(a * f(key) + b), 0, L-1) with the monotone feature
+// f(key) = fp32(bits(fp32(key))).  Leaf j: bucket = base_j +
+// clamp(floor(slope_j * fp32(key - xmin_j) + icpt_j), 0, width_j - 1).  All
+// fp32 operations are explicitly round-to-nearest and unfused, so results
+// are identical to any IEEE implementation of the same steps.
+// ---------------------------------------------------------------------------
+struct LearnedLeaf {
+  uint64_t xmin;
+  float slope;
+  float icpt;
+  uint32_t base;
+  uint32_t width;
+};
+static_assert(sizeof(LearnedLeaf) == 24, "leaf layout");
+constexpr uint32_t kModelMagic = 0x4D4C4748u;  // "HGLM"
+constexpr size_t kModelHeaderBytes = 32;
+
+__device__ __forceinline__ float rmi_feature(uint32_t key) {
+  return __uint2float_rn(__float_as_uint(__uint2float_rn(key)));
+}
+__device__ __forceinline__ float rmi_feature(uint64_t key) {
+  return __uint2float_rn(__float_as_uint(__ull2float_rn(key)));
+}
+
+struct LearnedMap {
+  const uint8_t* blob;  // device pointer
+  uint64_t Vcap;        // buckets of the table being built (host-provided bound)
+  float a, b;
+  uint32_t L;
+  uint64_t V;
+  const LearnedLeaf* leaves;
+  __device__ __forceinline__ void init() {
+    L = __ldg((const uint32_t*)(blob + 4));
+    V = __ldg((const unsigned long long*)(blob + 8));
+    a = __ldg((const float*)(blob + 16));
+    b = __ldg((const float*)(blob + 20));
+    leaves = (const LearnedLeaf*)(blob + kModelHeaderBytes);
+  }
+  template <typename K>
+  __device__ __forceinline__ uint32_t leaf_of(K key) const {
+    float r = __fadd_rn(__fmul_rn(a, rmi_feature(key)), b);
+    if (!(r >= 0.0f)) return 0;
+    if (r >= __uint2float_rn(L)) return L - 1;
+    return (uint32_t)r;
+  }
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K key) const {
+    const LearnedLeaf* lf = leaves + leaf_of(key);
+    uint64_t xmin = __ldg((const unsigned long long*)&lf->xmin);
+    float slope = __ldg(&lf->slope), icpt = __ldg(&lf->icpt);
+    uint32_t base = __ldg(&lf->base), width = __ldg(&lf->width);
+    uint32_t local = 0;
+    if (width > 0) {
+      uint64_t k = (uint64_t)key;
+      uint64_t d = k > xmin ? k - xmin : 0ull;
+      float p = __fadd_rn(__fmul_rn(slope, __ull2float_rn(d)), icpt);
+      if (!(p >= 0.0f)) local = 0;
+      else if (p >= __uint2float_rn(width)) local = width - 1;
+      else local = min((uint32_t)p, width - 1);
+    }
+    const uint64_t vmax = V < Vcap ? V : Vcap;
+    const uint64_t bk = (uint64_t)base + local;
+    return (uint32_t)(bk < vmax ? bk : vmax - 1);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Device status word (first bytes of every workspace).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t code) {
+  if (st) atomicCAS(st, 0u, code);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Scans.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(kFull, v, o);
+    if ((int)lane_id() >= o) v += u;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Exclusive block scan of one value per thread.  wsum: smem[32].  Returns
+// the exclusive prefix; *total receives the block sum.  Contains two
+// __syncthreads and leaves wsum reusable after a third.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* wsum, T* total) {
+  const int lane = lane_id(), w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  T incl = warp_incl_scan(v);
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    T x = lane < nw ? wsum[lane] : T(0);
+    x = warp_incl_scan(x);
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  T base = (w ? wsum[w - 1] : T(0)) + incl - v;
+  if (total) *total = wsum[nw - 1];
+  __syncthreads();
+  return base;
+}
+
+// In-place exclusive scan of a[0..m) in shared memory by the whole block
+// (sums carried in 32 bits).  Returns the total.  wsum: smem u32[32].
+template <typename T>
+__device__ __forceinline__ uint32_t block_excl_scan_smem(T* a, int m, uint32_t* wsum) {
+  const int nt = blockDim.x;
+  const int per = (m + nt - 1) / nt;
+  const int b = threadIdx.x * per;
+  const int e = min(b + per, m);
+  uint32_t s = 0;
+  for (int i = b; i < e; ++i) s += (uint32_t)a[i];
+  uint32_t total;
+  uint32_t base = block_excl_scan<uint32_t>(s, wsum, &total);
+  for (int i = b; i < e; ++i) {
+    const uint32_t x = (uint32_t)a[i];
+    a[i] = (T)base;
+    base += x;
+  }
+  __syncthreads();
+  return total;
+}
+
+// ---------------------------------------------------------------------------
+// Stable block-wide ranking by a small digit (ndig <= 256).
+//
+// The block's element sequence (length n <= NW*32*IPT) is split into NW
+// contiguous warp segments of 32*IPT elements; in round r lane l of warp w
+// holds element w*32*IPT + r*32 + l.  Inside a warp, equal digits of one
+// round are grouped with __match_any_sync and ranked by lane; a per-(digit,
+// warp) counter carries the running count from round to round, so ranks
+// follow the sequence order.  An exclusive scan of the counters in
+// digit-major, warp-minor order then gives every (digit, warp) its base in
+// the stably sorted sequence.
+//   dig[r]   digit of the element held in round r (ignored when invalid)
+//   dest[r]  out: position of that element in the stably sorted sequence
+//   wc       smem CT[ndig*NW] (scratch; CT = uint16_t when n < 65536)
+//   dstart   smem u32[ndig] out: first sorted position of each digit (or null)
+//   wsum     smem u32[32] (scratch)
+// Contains __syncthreads; every thread of the block must call it.
+// ---------------------------------------------------------------------------
+template <int IPT, int NW, typename CT>
+__device__ __forceinline__ void block_stable_rank(const uint32_t (&dig)[IPT], uint32_t n,
+                                                  uint32_t (&dest)[IPT], int ndig, CT* wc,
+                                                  uint32_t* dstart, uint32_t* wsum) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int m = ndig * NW;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) wc[i] = 0;
+  __syncthreads();
+  const uint32_t seg0 = (uint32_t)w * (32u * IPT);
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+    if (seg0 + (uint32_t)r * 32u < n) {  // warp-uniform
+      const bool valid = idx < n;
+      const uint32_t d = valid ? dig[r] : (0x10000u + lane);
+      const uint32_t peers = __match_any_sync(kFull, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (valid && lane == leader) {
+        old = (uint32_t)wc[d * NW + w];
+        wc[d * NW + w] = (CT)(old + __popc(peers));
+      }
+      old = __shfl_sync(kFull, old, leader);
+      dest[r] = old + __popc(peers & lt);
+      __syncwarp();
+    } else {
+      dest[r] = 0;
+    }
+  }
+  __syncthreads();
+  block_excl_scan_smem(wc, m, wsum);
+  if (dstart)
+    for (int d = threadIdx.x; d < ndig; d += blockDim.x) dstart[d] = (uint32_t)wc[d * NW];
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+    if (idx < n) dest[r] += (uint32_t)wc[dig[r] * NW + w];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies (cp.async.bulk) into shared memory with mbarrier
+// completion, and bounded waits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Wait for phase `parity` of `bar`, giving up after kWaitLimitNs.  Returns a
+// block-uniform verdict (every thread must call).  On failure it records
+// HG_ERR_TIMEOUT, waits once more (bounded) so that no copy is still landing
+// in shared memory, and the caller must return.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ bool mbar_wait_block(uint64_t* bar, uint32_t parity, uint32_t* status) {
+  bool ok = mbar_try_wait(bar, parity);
+  if (!ok) {
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+      if (mbar_try_wait(bar, parity)) {
+        ok = true;
+        break;
+      }
+      if ((it & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) break;
+    }
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok) {
+    set_status(status, HG_ERR_TIMEOUT);
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t0 < kWaitLimitNs) {
+    }
+  }
+  return ok;
+}
+
+// Copy elements [k0, k1) of a device array (element size ES bytes) into
+// smem so that smem[x - a0] holds element x for x in [a0, k1), where a0 is
+// k0 rounded down to a 16-byte boundary.  The 16-byte-aligned body goes
+// through one TMA bulk copy (issued by thread 0 together with the barrier's
+// expected byte count); the unaligned tail (< 16 bytes) is loaded by the
+// caller with load_tail() after the wait.  Returns a0.
+template <int ES>
+struct TileSpan {
+  uint64_t a0;     // first element in smem (16-byte aligned)
+  uint64_t body;   // elements copied by TMA: [a0, a0 + body)
+  uint64_t end;    // k1
+  __device__ __forceinline__ uint32_t bytes() const { return (uint32_t)(body * ES); }
+};
+template <int ES>
+__device__ __forceinline__ TileSpan<ES> tile_span(uint64_t k0, uint64_t k1) {
+  constexpr uint64_t per = 16 / ES;
+  TileSpan<ES> s;
+  s.a0 = k0 / per * per;
+  uint64_t b1 = k1 / per * per;
+  s.body = b1 > s.a0 ? b1 - s.a0 : 0;
+  s.end = k1;
+  return s;
+}
+template <int ES, typename T>
+__device__ __forceinline__ void load_tail(T* smem, const T* g, const TileSpan<ES>& s) {
+  for (uint64_t x = s.a0 + s.body + threadIdx.x; x < s.end; x += blockDim.x)
+    smem[x - s.a0] = g[x];
+}
+
+}  // namespace hg

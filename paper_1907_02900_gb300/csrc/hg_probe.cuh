@@ -1,0 +1,17 @@
+// Probe launch declaration.
+#pragma once
+
+#include <algorithm>
+
+#include "hg_device.cuh"
+
+namespace hg {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeQPT = 4;
+
+template <typename K, typename Map>
+hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck, uint32_t* out,
+                       cudaStream_t st, Map map);
+
+}  // namespace hg

@@ -1,0 +1,89 @@
+"""The C ABI library loads and exports every entry point its headers declare;
+argument errors are reported synchronously (no device work is issued)."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(header).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hg[a-z]*_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libs():
+    from paper_1907_02900_gb300 import _build
+    return _build.build()
+
+
+def _lib_for(header, libs):
+    base = os.path.basename(header)
+    return libs["libhg_datagen.so"] if base.startswith("hgd") else libs["libhg.so"]
+
+
+def test_every_declared_symbol_is_exported(libs):
+    headers = glob.glob(os.path.join(ROOT, "include", "*.h"))
+    assert headers
+    for h in headers:
+        names = _declared(h)
+        assert names, h
+        lib = _lib_for(h, libs)
+        out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+        exported = set(re.findall(r" T (\w+)", out))
+        missing = [n for n in names if n not in exported]
+        assert not missing, f"{os.path.basename(h)}: not exported by {os.path.basename(lib)}: {missing}"
+        dl = ctypes.CDLL(lib)
+        for n in names:
+            assert getattr(dl, n) is not None
+
+
+def test_status_strings_and_version(libs):
+    import paper_1907_02900_gb300 as hg
+    lib = hg.load()
+    assert b"sm_103a" in lib.hg_version()
+    for code in range(8):
+        assert lib.hg_status_string(code)
+
+
+def test_argument_errors_return_synchronously(libs):
+    import paper_1907_02900_gb300 as hg
+    lib = hg.load()
+    cfg = hg.make_config(hg.KEY_U32, 1 << 10)
+    fake = ctypes.c_void_p(0x10000)
+    # null config
+    assert lib.hg_build(None, fake, None, 10, fake, fake, fake, fake, 1 << 30, None) == 1
+    # bad key type / bucket count
+    bad = hg.make_config(hg.KEY_U32, 1 << 10); bad.key_type = 7
+    assert lib.hg_build(ctypes.byref(bad), fake, None, 10, fake, fake, fake, fake, 1 << 30, None) == 1
+    bad = hg.make_config(hg.KEY_U32, 0)
+    assert lib.hg_build(ctypes.byref(bad), fake, None, 10, fake, fake, fake, fake, 1 << 30, None) == 1
+    bad = hg.make_config(hg.KEY_U32, (1 << 32) + 1)
+    assert lib.hg_build(ctypes.byref(bad), fake, None, 10, fake, fake, fake, fake, 1 << 30, None) == 1
+    # n >= 2^32
+    assert lib.hg_build(ctypes.byref(cfg), fake, None, 1 << 32, fake, fake, fake, fake, 1 << 30, None) == 1
+    # misaligned keys
+    mis = ctypes.c_void_p(0x10004)
+    assert lib.hg_build(ctypes.byref(cfg), mis, None, 10, fake, fake, fake, fake, 1 << 30, None) == 1
+    # learned map without a model
+    lm = hg.make_config(hg.KEY_U64, 1 << 10); lm.map = hg.MAP_LEARNED
+    assert lib.hg_build(ctypes.byref(lm), fake, None, 10, fake, fake, fake, fake, 1 << 30, None) == 6
+    # probe with a null table, join with a null table
+    assert lib.hg_probe(ctypes.byref(cfg), None, fake, 10, fake, None) == 1
+    assert lib.hg_join_count(ctypes.byref(cfg), None, None, fake, None, fake, 1 << 20, None) == 1
+
+
+def test_workspace_sizes_cover_intermediate_arrays(libs):
+    import paper_1907_02900_gb300 as hg
+    for kt, kb in ((hg.KEY_U32, 4), (hg.KEY_U64, 8)):
+        for n, V in ((1 << 20, 1 << 20), (1 << 28, 1 << 30), (1000, 1), (5, 1 << 24)):
+            sz = hg.build_workspace_size(hg.make_config(kt, V), n)
+            assert sz >= n * (kb + 4), (kt, n, V)
+        v1 = hg.build_workspace_size(hg.make_config(kt, 1 << 20, algo="v1"), 1 << 20)
+        assert v1 >= (1 << 20) * 4

@@ -1,0 +1,135 @@
+"""Parity of the CUDA build and probe with the CPU oracle, bit for bit."""
+import numpy as np
+import pytest
+
+from paper_1907_02900_gb300 import datagen as dg
+from gpu_util import sampled_reference, table_np, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_build(hg, orc, keys, V, seed=0, algo="auto", bin_shift=0, ids=None):
+    t = hg.build(to_dev(keys), V, ids=None if ids is None else to_dev(ids), seed=seed, algo=algo,
+                 bin_shift=bin_shift)
+    off, ck, ci = table_np(t)
+    roff, rk, ri = orc.build(keys, V, seed, ids=ids)
+    assert np.array_equal(off, roff), "offsets differ"
+    assert np.array_equal(ck, rk), "csr keys differ"
+    assert np.array_equal(ci, ri), "csr ids differ"
+    return t
+
+
+@pytest.mark.parametrize("algo", ["v2", "v1"])
+@pytest.mark.parametrize("n,V", [(1, 1), (33, 7), (1000, 1), (4096, 4096), (100_000, 100_003),
+                                 ((1 << 20) + 37, 1 << 20), ((1 << 20) + 5, 1 << 16), (300_000, 1 << 22)])
+def test_build_u32_uniform(hg, orc, algo, n, V):
+    _check_build(hg, orc, dg.uniform_keys_u32(n, 1), V, seed=3, algo=algo)
+
+
+@pytest.mark.parametrize("bin_shift", [1, 4, 8, 12, 15])
+def test_build_v2_any_bin_size_same_table(hg, orc, bin_shift):
+    # Section 5.1: V1 and V2 produce the same table; with the canonical order
+    # the bytes are identical for every bin size.
+    _check_build(hg, orc, dg.uniform_keys_u32(200_000, 2), 1 << 18, algo="v2", bin_shift=bin_shift)
+
+
+def test_build_explicit_ids(hg, orc):
+    keys = dg.uniform_keys_u32(50_000, 4)
+    ids = (np.arange(50_000, dtype=np.uint32) * 2654435761 % (1 << 32)).astype(np.uint32)
+    for algo in ("v1", "v2"):
+        _check_build(hg, orc, keys, 1 << 15, algo=algo, ids=ids)
+
+
+@pytest.mark.parametrize("algo", ["v2", "v1"])
+def test_build_u64(hg, orc, algo):
+    _check_build(hg, orc, dg.uniform_keys_u64(300_001, 5), 1 << 18, seed=11, algo=algo)
+
+
+@pytest.mark.parametrize("algo", ["v2", "v1"])
+@pytest.mark.parametrize("mult", [4, 32, 1000, 100_000])
+def test_build_duplicates(hg, orc, algo, mult):
+    # Fig. "dup-keys": keys drawn from [1 .. N/d]; heavy buckets and bins
+    # larger than shared memory.
+    _check_build(hg, orc, dg.dup_keys_u32(400_000, mult, 6), 1 << 19, algo=algo)
+
+
+def test_build_all_keys_equal_and_single_bucket(hg, orc):
+    keys = np.full(70_000, 123456789, dtype=np.uint32)
+    for algo in ("v1", "v2"):
+        _check_build(hg, orc, keys, 1 << 16, algo=algo)
+        _check_build(hg, orc, dg.uniform_keys_u32(70_000, 8), 1, algo=algo)
+
+
+def test_build_zipf_u64(hg, orc):
+    keys = dg.zipf_keys_u64(1 << 20, 1 << 16, 7)
+    for algo in ("v2", "v1"):
+        _check_build(hg, orc, keys, 1 << 20, algo=algo)
+
+
+def test_build_sequence_input(hg, orc):
+    _check_build(hg, orc, dg.sequence_keys_u32(1 << 21), 1 << 20)
+
+
+def test_build_empty(hg):
+    import torch
+    t = hg.build(torch.empty(0, dtype=torch.uint32, device="cuda"), 17)
+    assert np.all(to_np(t.offsets) == 0)
+
+
+@pytest.mark.parametrize("hit", [0.0, 0.5, 1.0])
+def test_probe_u32(hg, orc, hit):
+    keys = dg.dup_keys_u32(300_000, 2, 9)
+    q = dg.queries_u32(200_000, keys, hit, 10)
+    V = 1 << 18
+    t = hg.build(to_dev(keys), V, seed=5)
+    got = to_np(hg.probe(t, to_dev(q)))
+    off, ck, _ = orc.build(keys, V, 5)
+    assert np.array_equal(got, orc.probe(off, ck, q, V, 5))
+    assert np.array_equal(got, orc.multiplicity(keys, q))
+
+
+def test_probe_u64_long_buckets(hg, orc):
+    keys = dg.zipf_keys_u64(200_000, 5000, 12)
+    q = dg.queries_u64(100_000, keys, 0.5, 13)
+    t = hg.build(to_dev(keys), 1 << 10)
+    assert np.array_equal(to_np(hg.probe(t, to_dev(q))), orc.multiplicity(keys, q))
+
+
+def test_probe_empty_queries_and_table(hg):
+    import torch
+    t = hg.build(to_dev(dg.uniform_keys_u32(1000, 1)), 64)
+    assert hg.probe(t, torch.empty(0, dtype=torch.uint32, device="cuda")).numel() == 0
+    e = hg.build(torch.empty(0, dtype=torch.uint32, device="cuda"), 64)
+    assert np.all(to_np(hg.probe(e, to_dev(dg.uniform_keys_u32(100, 2)))) == 0)
+
+
+def test_full_size_build_and_probe_sampled(hg, orc):
+    # 2^28 uint32 keys, V = 2^28 (load factor 1), the benchmark's launch
+    # configuration.  The whole offsets array and 2000 sampled buckets are
+    # checked against the oracle's definitions; probe counts of 20000 sampled
+    # queries against their multiplicity.
+    import torch
+    n = V = 1 << 28
+    keys = dg.uniform_keys_u32(n, dg.SEED_SCALE)
+    dk = to_dev(keys)
+    t = hg.build(dk, V)
+    rng = np.random.default_rng(0)
+    sample = np.unique(rng.integers(0, V, 2000))
+    roff, segs, b = sampled_reference(orc, keys, V, 0, sample)
+    off = to_np(t.offsets)
+    assert np.array_equal(off, roff)
+    ck, ci = t.keys, t.ids
+    for v, (rk, ri) in segs.items():
+        s, e = int(off[v]), int(off[v + 1])
+        assert np.array_equal(to_np(ck[s:e]), rk) and np.array_equal(to_np(ci[s:e]), ri)
+    q = dg.queries_u32(1 << 28, keys, 0.5, dg.SEED_SCALE + 1)
+    counts = to_np(hg.probe(t, to_dev(q)))
+    qi = rng.integers(0, len(q), 20000)
+    qs = q[qi]
+    qb = orc.buckets(qs, V)
+    # multiplicity of each sampled query: count equal keys inside its bucket
+    _, segq, _ = sampled_reference(orc, keys, V, 0, np.unique(qb))
+    want = np.array([int((segq[int(bb)][0] == x).sum()) for x, bb in zip(qs, qb)], dtype=np.uint32)
+    assert np.array_equal(counts[qi], want)
+    del t, dk
+    torch.cuda.empty_cache()

@@ -1,0 +1,73 @@
+"""Parity of Alg. 3 (bucket-wise intersection) with the CPU oracle."""
+import numpy as np
+import pytest
+
+from paper_1907_02900_gb300 import datagen as dg
+from gpu_util import to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _tables(hg, orc, a, b, V, seed=0):
+    tA = hg.build(to_dev(a), V, seed=seed)
+    tB = hg.build(to_dev(b), V, seed=seed)
+    rA = orc.build(a, V, seed)
+    rB = orc.build(b, V, seed)
+    return tA, tB, rA, rB
+
+
+@pytest.mark.parametrize("V", [1, 64, 4096, 1 << 17])
+def test_join_count_u32(hg, orc, V):
+    a = dg.dup_keys_u32(120_000, 3, 1)
+    b = dg.dup_keys_u32(90_000, 2, 2)
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V, seed=4)
+    total, per = hg.join_count(tA, tB)
+    rt, rper = orc.join_count(rA[0], rA[1], rB[0], rB[1], V)
+    assert int(total.item()) == rt == orc.join_size_by_keys(a, b)
+    assert np.array_equal(to_np(per), rper)
+
+
+def test_join_count_zipf_u64(hg, orc):
+    # Section 5 join workload shape: Zipf(1) build side vs uniform probe side.
+    a = dg.zipf_keys_u64(1 << 20, 1 << 17, 3)
+    b = dg.uniform_domain_keys_u64(1 << 20, 1 << 17, 4)
+    V = 1 << 20
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V)
+    total, per = hg.join_count(tA, tB)
+    rt, rper = orc.join_count(rA[0], rA[1], rB[0], rB[1], V)
+    assert int(total.item()) == rt
+    assert np.array_equal(to_np(per), rper)
+
+
+@pytest.mark.parametrize("V", [1, 512, 1 << 16])
+def test_join_materialize_canonical_order(hg, orc, V):
+    a = dg.zipf_keys_u64(60_000, 4000, 5)
+    b = dg.uniform_domain_keys_u64(50_000, 4000, 6)
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V, seed=2)
+    pa, pb = hg.join_materialize(tA, tB)
+    ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V)
+    assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
+
+
+def test_join_materialize_capacity_overflow(hg, orc):
+    a = dg.dup_keys_u32(20_000, 10, 7)
+    b = dg.dup_keys_u32(20_000, 10, 8)
+    V = 1 << 12
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V)
+    total = int(hg.join_count(tA, tB)[0].item())
+    cap = total // 3
+    pa, pb = hg.join_materialize(tA, tB, capacity=cap)
+    ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V, cap=cap)
+    assert len(pa) == cap
+    assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
+
+
+def test_join_empty_sides(hg):
+    import torch
+    e = torch.empty(0, dtype=torch.uint32, device="cuda")
+    tA = hg.build(e, 32)
+    tB = hg.build(to_dev(dg.uniform_keys_u32(1000, 1)), 32)
+    assert int(hg.join_count(tA, tB)[0].item()) == 0
+    assert int(hg.join_count(tB, tA)[0].item()) == 0
+    pa, pb = hg.join_materialize(tB, tA)
+    assert pa.numel() == 0
