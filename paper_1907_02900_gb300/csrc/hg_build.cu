@@ -46,7 +46,7 @@ size_t bin_smem_bytes(int kb, uint32_t emax) {
 }
 
 size_t big_smem_bytes(int kb, uint32_t nb) {
-  size_t b = (size_t)nb * 4 + (size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2 + 256 * kBinNW * 2;
+  size_t b = align_up((size_t)nb * 4, 16) + (size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2 + 256 * kBinNW * 2;
   return align_up(b, 16) + 32 * 4 + 64;
 }
 
@@ -72,6 +72,7 @@ bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
     const double bpb = n ? target * (double)V / (double)n : (double)V;
     s = bpb <= 1.0 ? 0 : (int)std::floor(std::log2(bpb));
   }
+  if (!cfg->bin_shift) s = std::min(s, (int)kMaxBinShift);
   s = std::max(s, ceil_log2_u64(V) - (int)kMaxBinsLog2);
   s = std::max(s, 0);
   if (s > (int)kMaxBinShift) return false;
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
   map.init();
   const uint32_t nbmax = 1u << a.s;
   uint8_t* sp = smem;
-  uint32_t* cur = (uint32_t*)sp; sp += (size_t)nbmax * 4;
+  uint32_t* cur = (uint32_t*)sp; sp += align_up((size_t)nbmax * 4, 16);
   K* tk = (K*)sp; sp += (size_t)kBigTile * sizeof(K);
   uint32_t* ti = (uint32_t*)sp; sp += (size_t)kBigTile * 4;
   uint16_t* lb = (uint16_t*)sp; sp += kBigTile * 2;
@@ -725,17 +726,20 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     HG_TRACE("k_colscan", st);
     k_colscan<<<(p.nsb + 255) / 256, 256, 0, st>>>(C, p.G, p.nsb, CT);
   }
+  const bool two = p.sshift > 0;
   {
     HG_TRACE("k_scan_bins", st);
     k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, p.emax, ovf, &hdr->ovf_count, offsets, p.V, (uint32_t)p.n);
   }
 
-  const bool two = p.sshift > 0;
   PartArgs<K> pa{};
   pa.in_k = keys;
   pa.in_i = ids;
-  pa.out_k = csr_k;  // pass A output lives in the caller's CSR arrays until pass B
-  pa.out_i = csr_i;
+  // With two partition passes, pass A's output lives in the caller's CSR
+  // arrays until pass B has read it; with one pass it goes straight to the
+  // workspace, so that no bin build reads and writes the same region.
+  pa.out_k = two ? csr_k : bk;
+  pa.out_i = two ? csr_i : bi;
   pa.n = p.n;
   pa.chunk = p.chunk;
   pa.G = p.G;
@@ -776,8 +780,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     }
   }
   BinArgs<K> ba{};
-  ba.in_k = two ? bk : csr_k;
-  ba.in_i = two ? bi : csr_i;
+  ba.in_k = bk;
+  ba.in_i = bi;
   ba.csr_k = csr_k;
   ba.csr_i = csr_i;
   ba.offsets = offsets;

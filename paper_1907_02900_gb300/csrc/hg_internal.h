@@ -20,6 +20,9 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 256, "workspace header");
 
 constexpr size_t kAlign = 256;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 
 // Device properties cached per device.

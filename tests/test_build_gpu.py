@@ -35,7 +35,7 @@ def test_build_v2_any_bin_size_same_table(hg, orc, bin_shift):
 
 def test_build_explicit_ids(hg, orc):
     keys = dg.uniform_keys_u32(50_000, 4)
-    ids = (np.arange(50_000, dtype=np.uint32) * 2654435761 % (1 << 32)).astype(np.uint32)
+    ids = (np.arange(50_000, dtype=np.uint64) * np.uint64(2654435761) % np.uint64(1 << 32)).astype(np.uint32)
     for algo in ("v1", "v2"):
         _check_build(hg, orc, keys, 1 << 15, algo=algo, ids=ids)
 
