@@ -129,6 +129,28 @@ hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_
                               int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
                               int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------ build, no allocation --
+ * The paper has no counterpart of this entry point.  It is hg_build (V2)
+ * for callers that cannot allocate device memory -- code running inside a
+ * host runtime that owns all device memory and offers no allocator, or a
+ * serving loop that bans cudaMalloc/cudaFree because they can synchronise
+ * the device.  Inputs and outputs are still the caller's; the scratch space
+ * is a fixed device array inside the library, hg_static_scratch_bytes()
+ * bytes (8 MiB) per GPU that loads the library, held until the process exits.
+ *   Same arguments and results as hg_build, without the workspace.
+ *   Requests whose V2 plan needs more scratch than the array holds (more
+ *   than hg_static_scratch_bytes() from hg_build_workspace_size; up to 2^18
+ *   keys always fit for V <= 2^29) return HG_ERR_WORKSPACE_TOO_SMALL;
+ *   cfg->algo == HG_ALGO_V1 returns HG_ERR_UNSUPPORTED.
+ *   The first call on a device looks up the array's device address; make it
+ *   before any stream capture.  All calls share the one array and it keeps
+ *   the last call's contents: calls whose GPU work overlaps race, so
+ *   serialise them (one stream, or host-side ordering). */
+size_t hg_static_scratch_bytes(void);
+hg_status hg_build_static_scratch(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids,
+                                  uint64_t n, uint32_t* d_offsets, void* d_csr_keys,
+                                  uint32_t* d_csr_ids, void* stream);
+
 /* --------------------------------------------------------------- status --
  * Device status word of a workspace (HG_OK when no device-side error was
  * recorded).  Synchronises `stream` first.  hg_workspace_clear resets it. */

@@ -22,7 +22,7 @@ NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler"
            "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 LIBS = {
-    "libhg.so": ["hg_build.cu", "hg_probe.cu", "hg_join.cu", "hg_learned.cu", "hg_batch.cu", "hg_trace.cu", "hg_api.cu"],
+    "libhg.so": ["hg_build.cu", "hg_probe.cu", "hg_join.cu", "hg_learned.cu", "hg_batch.cu", "hg_trace.cu", "hg_static.cu", "hg_api.cu"],
     "libhg_datagen.so": ["hg_datagen.cu"],
 }
 
