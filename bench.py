@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--log2v", type=int, default=None)
     ap.add_argument("--hit", type=float, default=0.5)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--standard-probe", action="store_true", help="time HashGraph-Probe-Standard instead of the binned probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
     return ap.parse_args()
@@ -146,16 +147,32 @@ def recorded_traffic(kernel: str, n: int, V: int):
 # --------------------------------------------------------------------------
 # algorithmic bytes of each kernel (per launch) for the uint32 workload
 # --------------------------------------------------------------------------
-def algorithmic_bytes(kb: int, n: int, V: int, q: int, hit: float) -> dict:
+PROBE_KERNELS = {"k_hist_Q", "k_colscan_Q", "k_scan_Q", "k_partition_Q", "k_probe", "k_unpermute"}
+
+
+def algorithmic_bytes(kb: int, n: int, V: int, q: int, hit: float, binned: bool = True) -> dict:
+    """Bytes each kernel must move per launch (reads + writes of its inputs and
+    outputs at element granularity; the standard probe at 32-byte-sector
+    granularity for its random reads)."""
     alpha = n / V
     nonempty = hit + (1.0 - hit) * (1.0 - math.exp(-alpha))
-    return {
+    table = 4 * (V + 1) + kb * n
+    out = {
         "k_hist": kb * n,                                  # read keys
         "k_partition_A": kb * n + (kb + 4) * n,            # read keys, write (key, id)
         "k_partition_B": 2 * (kb + 4) * n,                 # read and write (key, id)
         "k_binbuild": 2 * (kb + 4) * n + 4 * V,            # read (key, id), write CSR + offsets
-        "k_probe": q * (kb + 4) + q * 32 + q * 32 * nonempty,  # 32 B sectors: offsets, first key
     }
+    if binned:
+        out.update({
+            "k_hist_Q": kb * q,                            # read queries
+            "k_partition_Q": kb * q + (kb + 4) * q,        # read queries, write (query, position)
+            "k_probe": kb * q + 4 * q + table,             # read grouped queries, write counts, table once
+            "k_unpermute": 3 * 4 * q,                      # read (position, count), write counts
+        })
+    else:
+        out["k_probe"] = q * (kb + 4) + q * 32 + q * 32 * nonempty  # 32 B sectors: offsets, first key
+    return out
 
 
 def oracle_sample(log2n: int, log2v: int, hit: float, seed: int):
@@ -245,10 +262,15 @@ def run_hg(args):
     counts = torch.empty(q, dtype=torch.uint32, device=dev)
     table = hg.Table(offsets, ck, ci, cfg)
     stream = torch.cuda.current_stream()
+    binned = not args.standard_probe
+    pws = torch.empty(max(hg.probe_workspace_size(table, q), 1), dtype=torch.uint8, device=dev) if binned else None
 
     def step(kd, qd):
         hg.build_into(cfg, kd, None, offsets, ck, ci, ws, stream)
-        hg.probe_into(table, qd, counts, stream)
+        if binned:
+            hg.probe_binned_into(table, qd, counts, pws, stream)
+        else:
+            hg.probe_into(table, qd, counts, stream)
 
     for _ in range(args.warmup):
         step(keys_d, q_d)
@@ -292,7 +314,7 @@ def run_hg(args):
     # per-kernel breakdown and the dominant kernel's roofline
     peaks, peak_src = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    algo = algorithmic_bytes(4, n, V, q, args.hit)
+    algo = algorithmic_bytes(4, n, V, q, args.hit, binned)
     phases = {}
     for k, (ms, c) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
         avg = ms / max(c, 1)
@@ -310,8 +332,8 @@ def run_hg(args):
         roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1) if ach else None, "peak": hbm,
                 "unit": "GB/s", "frac": round(ach / hbm, 4) if ach else None,
                 "traffic": recorded_traffic(dom, n, V), "peak_source": f"hbm_gbs of {peak_src}"}
-    build_ms = sum(prof[k][0] for k in prof if k != "k_probe") / args.steps
-    probe_ms = prof.get("k_probe", (0.0, 1))[0] / args.steps
+    build_ms = sum(prof[k][0] for k in prof if k not in PROBE_KERNELS) / args.steps
+    probe_ms = sum(prof[k][0] for k in prof if k in PROBE_KERNELS) / args.steps
 
     # end to end through the public API with host buffers
     e2e = None
@@ -361,7 +383,11 @@ def run_hg(args):
                        "parallelism": f"replicas x{world} (independent tables per GPU)"},
             "build_gkeys_s": round(n / (build_ms * 1e-3) / 1e9, 3) if build_ms else None,
             "probe_gkeys_s": round(q / (probe_ms * 1e-3) / 1e9, 3) if probe_ms else None,
-            "end_to_end_min_bytes_frac": round((16 * n + 4 * V + algo["k_probe"]) / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
+            # the whole step against its minimum traffic: build 4N read + 8N CSR + 4V offsets written,
+            # probe 4Q read + 4Q written + the table read once
+            "end_to_end_min_bytes_frac": round((16 * n + 4 * V + 8 * q + 4 * (V + 1) + 4 * n)
+                                               / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
+            "probe": "binned" if binned else "standard",
             "roofline": roof, "phases": phases, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
         }

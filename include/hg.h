@@ -106,6 +106,19 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_i
 hg_status hg_probe(const hg_config* cfg, const hg_table* table, const void* d_queries, uint64_t q,
                    uint32_t* d_counts, void* stream);
 
+/* Binned probe: the same result as hg_probe (per-query match counts), for
+ * large query batches.  The queries are first partitioned by bucket range
+ * into at most 256 groups (the V2 build's histogram and stable partition
+ * applied to the queries), each group is probed while its slice of the table
+ * stays in L2, and the counts are merged back into query order.  Trades
+ * random DRAM reads (one burst per 4-byte read) for sequential passes.
+ *   d_queries must be 16-byte aligned; q < 2^32.
+ *   d_ws/ws_bytes: at least hg_probe_workspace_size(cfg, table->n, q) bytes. */
+size_t hg_probe_workspace_size(const hg_config* cfg, uint64_t table_n, uint64_t q);
+hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const void* d_queries,
+                          uint64_t q, uint32_t* d_counts, void* d_ws, size_t ws_bytes,
+                          void* stream);
+
 /* ----------------------------------------------------------------- join --
  * HashGraph-Probe-New (Alg. 3, Section 3.4): both inputs are built into
  * tables with the same V and map; bucket v of A is intersected with bucket v

@@ -58,6 +58,10 @@ SIGNATURES = {
     "hg_build_workspace_size": (_SZ, [_CFGP, _U64]),
     "hg_build": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_probe": (_I32, [_CFGP, _TABP, _VP, _U64, _VP, _VP]),
+    "hg_probe_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
+    "hg_probe_binned": (_I32, [_CFGP, _TABP, _VP, _U64, _VP, _VP, _SZ, _VP]),
+    "hg_static_scratch_bytes": (_SZ, []),
+    "hg_build_static_scratch": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
     "hg_join_count": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_join_materialize": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
@@ -101,7 +105,7 @@ def load(path: str | None = None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIBPATH
+    path = path or os.environ.get("HG_LIBHG") or LIBPATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with paper_1907_02900_gb300._build.build() "
                            "(or __graft_entry__.build()); there is no CPU fallback")
@@ -230,14 +234,40 @@ def probe_into(table: Table, queries, counts, stream=None):
     _check(rc, "hg_probe")
 
 
-def probe(table: Table, queries, stream=None):
-    """HashGraph-Probe-Standard: uint32 count of build keys equal to each query."""
+BINNED_PROBE_MIN_QUERIES = 1 << 20
+
+
+def probe_workspace_size(table: Table, q: int) -> int:
+    return int(load().hg_probe_workspace_size(ctypes.byref(table.cfg), table.keys.numel(), q))
+
+
+def probe_binned_into(table: Table, queries, counts, ws, stream=None):
+    """hg_probe_binned on caller-provided tensors (no allocation)."""
+    tv = table.view()
+    rc = load().hg_probe_binned(ctypes.byref(table.cfg), ctypes.byref(tv), _ptr(queries), queries.numel(),
+                                _ptr(counts), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_probe_binned")
+
+
+def probe(table: Table, queries, stream=None, binned: bool | None = None, ws=None):
+    """uint32 count of build keys equal to each query (HashGraph-Probe-Standard
+    semantics).  binned=None picks the binned probe for large batches."""
     torch = _torch()
     _require_cuda(queries, "queries")
     if _key_type_of(queries) != table.cfg.key_type:
         raise TypeError("query key type differs from the table's")
     counts = torch.empty(queries.numel(), dtype=torch.uint32, device=queries.device)
-    probe_into(table, queries, counts, stream)
+    if binned is None:
+        binned = queries.numel() >= BINNED_PROBE_MIN_QUERIES
+    if binned:
+        need = probe_workspace_size(table, queries.numel())
+        if need == 0:
+            raise HGError(7, "hg_probe_workspace_size")
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=queries.device)
+        probe_binned_into(table, queries, counts, ws, stream)
+    else:
+        probe_into(table, queries, counts, stream)
     return counts
 
 

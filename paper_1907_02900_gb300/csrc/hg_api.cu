@@ -134,7 +134,39 @@ hg_status hg_probe(const hg_config* cfg, const hg_table* table, const void* d_qu
   cudaStream_t st = (cudaStream_t)stream;
   return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
     using K = decltype(k);
-    return probe_launch<K>((const K*)d_queries, q, table->d_offsets, (const K*)table->d_keys, d_counts, st, map);
+    return probe_launch<K>((const K*)d_queries, q, table->d_offsets, (const K*)table->d_keys, d_counts,
+                           cfg->num_buckets, st, map);
+  });
+}
+
+size_t hg_probe_workspace_size(const hg_config* cfg, uint64_t table_n, uint64_t q) {
+  if (validate_config(cfg) != HG_OK) return 0;
+  ProbePlan p{};
+  if (!make_probe_plan(cfg, table_n, q, &p)) return 0;
+  return p.total;
+}
+
+hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const void* d_queries, uint64_t q,
+                          uint32_t* d_counts, void* d_ws, size_t ws_bytes, void* stream) {
+  hg_status rc = validate_config(cfg);
+  if (rc != HG_OK) return rc;
+  if (!table || !table->d_offsets || !d_ws) return HG_ERR_INVALID_ARG;
+  if (q >= (1ull << 32)) return HG_ERR_INVALID_ARG;
+  if (q > 0 && (!d_queries || !d_counts)) return HG_ERR_INVALID_ARG;
+  if (table->n > 0 && !table->d_keys) return HG_ERR_INVALID_ARG;
+  const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  if (!aligned(d_queries, 16) || !aligned(table->d_keys, kb) || !aligned(d_counts, 4) || !aligned(d_ws, 256))
+    return HG_ERR_INVALID_ARG;
+  ProbePlan p{};
+  if (!make_probe_plan(cfg, table->n, q, &p)) return HG_ERR_UNSUPPORTED;
+  if (ws_bytes < p.total) return HG_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+  if (q == 0) return HG_OK;
+  return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
+    using K = decltype(k);
+    return probe_binned_impl<K>(p, cfg->num_buckets, table, (const K*)d_queries, q, d_counts, (uint8_t*)d_ws, st,
+                                map);
   });
 }
 

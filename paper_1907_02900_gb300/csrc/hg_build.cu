@@ -22,6 +22,7 @@
 #include "hg_trace.h"
 #include "hg_partition.cuh"
 #include "hg_scan.cuh"
+#include "hg_probe.cuh"
 
 namespace hg {
 
@@ -34,27 +35,25 @@ static int ceil_log2_u64(uint64_t x) {
   return l;
 }
 
-template <typename K>
-static constexpr int bin_ipt() {
-  return sizeof(K) == 4 ? 9 : 7;
-}
-
-size_t bin_smem_bytes(int kb, uint32_t emax) {
-  // two staging buffers of keys and ids, three u16 position arrays, u16 warp counters
-  size_t b = 2 * (size_t)(emax + 16) * (kb + 4) + 3 * (size_t)emax * 2 + 256 * kBinNW * 2;
-  return align_up(b, 16) + 32 * 4 + 2 * 8 + 64;
+size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf) {
+  // staging buffers of keys and ids, lb and slot arrays (u16), packed u16
+  // bucket counters, heavy-bucket list
+  size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + 2 * (size_t)emax * 2 + (((size_t)1 << s) + 1) / 2 * 4 +
+             ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2;
+  return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
 }
 
 size_t big_smem_bytes(int kb, uint32_t nb) {
-  size_t b = align_up((size_t)nb * 4, 16) + (size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2 + 256 * kBinNW * 2;
-  return align_up(b, 16) + 32 * 4 + 64;
+  size_t b = align_up((size_t)nb * 4, 16) + (size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2;
+  return align_up(b, 16) + (size_t)rank_words<kBinNW>() * 4 + 32 * 4 + 64;
 }
 
-size_t part_smem_bytes(int kb, bool ids_in) {
-  size_t tile = kPartTile + 16;
-  size_t b = 2 * tile * kb + (ids_in ? 2 * tile * 4 : 0) + (size_t)kPartTile * (kb + 4 + 1) +
-             256 * kPartNW * 4 + 3 * 256 * 4;
-  return align_up(b, 16) + 32 * 4 + 2 * 8 + 64;
+size_t part_smem_bytes(int kb, bool ids_in, int ipt, bool item_list) {
+  const size_t tile = (size_t)kPartNW * 32 * ipt;
+  const size_t tb = tile + 16;
+  size_t b = 2 * tb * kb + (ids_in ? 2 * tb * 4 : 0) + tile * (kb + 4 + 1) + (size_t)rank_words<kPartNW>() * 4 +
+             2 * 256 * 4;
+  return align_up(b, 16) + (item_list ? 2 * kMaxItemsPerCta * 4 : 0) + 32 * 4 + 2 * 8 + 64;
 }
 
 bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
@@ -62,7 +61,7 @@ bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
   p->kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
   p->n = n;
   p->V = cfg->num_buckets;
-  p->emax = kBinNW * 32 * (p->kb == 4 ? bin_ipt<uint32_t>() : bin_ipt<uint64_t>());
+  p->emax = p->kb == 4 ? kBinEmaxU32 : kBinEmaxU64;
   const uint64_t V = p->V;
   int s;
   if (cfg->bin_shift) {
@@ -222,10 +221,13 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
 }
 
 // Phase 2 (both passes).  Pass A: items are input chunks; digit = super-bin.
-// Pass B: items are (super-bin, chunk) sub-ranges of pass A's output; digit =
-// bin inside the super-bin.  Tiles stream through shared memory by TMA bulk
-// copies, double-buffered; each tile is stably partitioned and written out
-// as contiguous runs.
+// Pass B: items are (super-bin, group of gg consecutive chunks) sub-ranges of
+// pass A's output, contiguous in memory; digit = bin inside the super-bin.
+// A group's elements are in input order, so one running cursor per bin,
+// started at the bin start plus the earlier chunks' counts, keeps the pass
+// stable.  Tiles stream through shared memory by TMA bulk copies,
+// double-buffered; each tile is stably partitioned and written out as
+// contiguous runs.
 template <typename K>
 struct PartArgs {
   const K* in_k;
@@ -234,6 +236,7 @@ struct PartArgs {
   uint32_t* out_i;
   uint64_t n, chunk;
   uint32_t G, s, sshift, nbins, nsb;
+  uint32_t gg, ngroups;  // pass B: chunks per item, items per super-bin
   const uint32_t* H;   // per (chunk, bin) exclusive column prefix
   const uint32_t* C;   // per (chunk, super-bin) exclusive column prefix
   const uint32_t* CT;  // per super-bin totals
@@ -241,10 +244,10 @@ struct PartArgs {
   uint32_t* status;
 };
 
-template <typename K, typename Map, bool PASS_B>
-__global__ void __launch_bounds__(kPartNW * 32, 2) k_partition(PartArgs<K> a, Map map) {
-  constexpr int IPT = kPartIPT, NW = kPartNW;
-  constexpr uint32_t TILE = kPartTile;
+template <typename K, typename Map, bool PASS_B, int IPT>
+__global__ void __launch_bounds__(kPartNW * 32, kPartMinBlocks) k_partition(PartArgs<K> a, Map map) {
+  constexpr int NW = kPartNW;
+  constexpr uint32_t TILE = NW * 32 * IPT;
   constexpr uint32_t TB = TILE + 16;
   const bool has_ids = PASS_B || a.in_i != nullptr;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -261,28 +264,39 @@ __global__ void __launch_bounds__(kPartNW * 32, 2) k_partition(PartArgs<K> a, Ma
   }
   K* sk = (K*)sp; sp += TILE * sizeof(K);
   uint32_t* sv = (uint32_t*)sp; sp += TILE * 4;
-  uint32_t* wc = (uint32_t*)sp; sp += 256 * NW * 4;
+  uint32_t* wc = (uint32_t*)sp; sp += rank_words<NW>() * 4;
   uint32_t* dstart = (uint32_t*)sp; sp += 256 * 4;
   uint32_t* cursor = (uint32_t*)sp; sp += 256 * 4;
-  uint32_t* scratch = (uint32_t*)sp; sp += 256 * 4;
   uint8_t* sd = sp; sp += TILE;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  uint32_t* ilo = (uint32_t*)sp; sp += PASS_B ? kMaxItemsPerCta * 4 : 0;
+  uint32_t* ihi = (uint32_t*)sp; sp += PASS_B ? kMaxItemsPerCta * 4 : 0;
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
   uint64_t* bar = (uint64_t*)sp;
-  (void)scratch;
 
   map.init();
-  const uint64_t nitems = PASS_B ? (uint64_t)a.nsb * a.G : (uint64_t)a.G;
+  for (int i = threadIdx.x; i < rank_words<NW>(); i += blockDim.x) wc[i] = 0;
+  const uint64_t nitems = PASS_B ? (uint64_t)a.nsb * a.ngroups : (uint64_t)a.G;
+  if (PASS_B) {
+    // input ranges of this CTA's items, gathered once (keeps global loads out
+    // of the tile loop's control path)
+    for (uint64_t j = threadIdx.x, item = blockIdx.x + j * gridDim.x; item < nitems;
+         j += blockDim.x, item = blockIdx.x + j * gridDim.x) {
+      const uint32_t sb = (uint32_t)(item / a.ngroups), grp = (uint32_t)(item % a.ngroups);
+      const uint32_t g0 = grp * a.gg, g1 = min(g0 + a.gg, a.G);
+      const uint32_t base = a.BS[sb << a.sshift];
+      ilo[j] = base + a.C[(uint64_t)g0 * a.nsb + sb];
+      ihi[j] = base + (g1 < a.G ? a.C[(uint64_t)g1 * a.nsb + sb] : a.CT[sb]);
+    }
+  }
   auto item_range = [&](uint64_t item, uint64_t& i0, uint64_t& i1) {
     if (!PASS_B) {
       i0 = item * a.chunk;
       i1 = min(i0 + a.chunk, a.n);
     } else {
-      const uint32_t sb = (uint32_t)(item / a.G), g = (uint32_t)(item % a.G);
-      const uint32_t c = a.C[(uint64_t)g * a.nsb + sb];
-      const uint32_t c_next = g + 1 < a.G ? a.C[(uint64_t)(g + 1) * a.nsb + sb] : a.CT[sb];
-      i0 = (uint64_t)a.BS[sb << a.sshift] + c;
-      i1 = i0 + (c_next - c);
+      const uint64_t j = (item - blockIdx.x) / gridDim.x;
+      i0 = ilo[j];
+      i1 = ihi[j];
     }
   };
   // Tile stream of this CTA: items blockIdx.x, +gridDim.x, ...; tiles of TILE.
@@ -338,29 +352,30 @@ __global__ void __launch_bounds__(kPartNW * 32, 2) k_partition(PartArgs<K> a, Ma
     if (nxt.ok) issue(nxt, buf ^ 1);
     if (!mbar_wait_block(&bar[buf], (it >> 1) & 1u, a.status)) return;
     const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(cur.t0, cur.t1);
-    load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
     TileSpan<4> si_{};
-    if (has_ids) {
-      si_ = tile_span<4>(cur.t0, cur.t1);
-      load_tail<4>(iin[buf], a.in_i, si_);
-    }
+    if (has_ids) si_ = tile_span<4>(cur.t0, cur.t1);
+    // elements past the last 16-byte boundary (only where a tile ends
+    // unaligned) come in by plain loads; the barrier is needed only then
+    bool sync_needed = (sk_.a0 + sk_.body < cur.t1) || (has_ids && si_.a0 + si_.body < cur.t1);
+    load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
+    if (has_ids) load_tail<4>(iin[buf], a.in_i, si_);
     uint32_t sb = 0;
-    if (PASS_B) sb = (uint32_t)(cur.item / a.G);
-    if (cur.item != cur_item) {
+    if (PASS_B) sb = (uint32_t)(cur.item / a.ngroups);
+    if (cur.item != cur_item) {  // cursors are first read after tile_partition_fast's first barrier
       cur_item = cur.item;
       if (!PASS_B) {
         ndig = (int)a.nsb;
         for (int d = threadIdx.x; d < ndig; d += blockDim.x)
           cursor[d] = a.BS[(uint32_t)d << a.sshift] + a.C[cur.item * a.nsb + d];
       } else {
-        const uint32_t g = (uint32_t)(cur.item % a.G);
+        const uint32_t g = (uint32_t)(cur.item % a.ngroups) * a.gg;
         const uint32_t b0 = sb << a.sshift;
         ndig = (int)min(1u << a.sshift, a.nbins - b0);
         for (int d = threadIdx.x; d < ndig; d += blockDim.x)
           cursor[d] = a.BS[b0 + d] + a.H[(uint64_t)g * a.nbins + b0 + d];
       }
     }
-    __syncthreads();
+    if (sync_needed) __syncthreads();  // block-uniform condition
     const uint32_t cnt = (uint32_t)(cur.t1 - cur.t0);
     const K* kk = kin[buf] + (cur.t0 - sk_.a0);
     const uint32_t* ii = has_ids ? iin[buf] + (cur.t0 - si_.a0) : nullptr;
@@ -380,8 +395,8 @@ __global__ void __launch_bounds__(kPartNW * 32, 2) k_partition(PartArgs<K> a, Ma
         dig[r] = 0;
       }
     }
-    tile_partition_out<K, IPT, NW>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
-                                   a.out_k, a.out_i);
+    tile_partition_fast<K, IPT, NW>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                    a.out_k, a.out_i);
     cur = nxt;
   }
 }
@@ -400,37 +415,62 @@ struct BinArgs {
   const uint32_t* BS;
   uint64_t V;
   uint32_t nbins, s, emax;
+  int nbuf;  // staging buffers: 2 = next bin prefetched during this one
   uint32_t* status;
 };
 
-template <typename K, typename Map, int IPT>
+// Per bin (E <= emax edges, nb local buckets):
+//   1. local bucket lb of every edge; bucket counts by shared-memory atomics
+//      (counts do not depend on order); two 16-bit counters per word
+//   2. exclusive scan of the counts -> the bin's CSR offsets (written out)
+//   3. every edge claims a slot of its bucket with an atomic increment; the
+//      slot order inside a bucket is arbitrary at this point
+//   4. every bucket sorts its slots by position in the bin, which is input
+//      order because both partition passes are stable: insertion sort for
+//      up to kBinSmallBucket edges, a per-warp position bitmap above
+//   5. the edges are written out in slot order (coalesced)
+template <typename K, typename Map>
 __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map map) {
-  constexpr int NW = kBinNW;
   const uint32_t EB = a.emax + 16;
+  const int nbuf = a.nbuf;
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sp = smem;
   K* kin[2];
   uint32_t* iin[2];
   kin[0] = (K*)sp; sp += (size_t)EB * sizeof(K);
-  kin[1] = (K*)sp; sp += (size_t)EB * sizeof(K);
+  kin[1] = kin[0];
+  if (nbuf == 2) { kin[1] = (K*)sp; sp += (size_t)EB * sizeof(K); }
   iin[0] = (uint32_t*)sp; sp += (size_t)EB * 4;
-  iin[1] = (uint32_t*)sp; sp += (size_t)EB * 4;
-  uint16_t* lb = (uint16_t*)sp; sp += (size_t)a.emax * 2;
-  uint16_t* tmp = (uint16_t*)sp; sp += (size_t)a.emax * 2;
-  uint16_t* perm = (uint16_t*)sp; sp += (size_t)a.emax * 2;
-  uint16_t* wc = (uint16_t*)sp; sp += 256 * NW * 2;
+  iin[1] = iin[0];
+  if (nbuf == 2) { iin[1] = (uint32_t*)sp; sp += (size_t)EB * 4; }
+  uint16_t* lb = (uint16_t*)sp; sp += (size_t)a.emax * 2;        // also the heavy-bucket bitmaps
+  uint16_t* opos = (uint16_t*)sp; sp += (size_t)a.emax * 2;
+  uint32_t* cnt = (uint32_t*)sp; sp += (((size_t)1 << a.s) + 1) / 2 * 4;
+  uint16_t* heavy = (uint16_t*)sp; sp += (size_t)(a.emax / (kBinSmallBucket + 1) + 2) * 2;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
+  uint32_t* nheavy = (uint32_t*)sp; sp += 16;
+  uint32_t* bl_start = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;  // this CTA's bins: start, size
+  uint32_t* bl_size = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;
   uint64_t* bar = (uint64_t*)sp;
 
   map.init();
-  auto skip = [&](uint32_t b) {
-    while (b < a.nbins && a.T[b] > a.emax) b += gridDim.x;
-    return b;
+  // Bins blockIdx.x, +gridDim.x, ...: starts and sizes gathered once, so the
+  // loop below needs no global loads to find its next bin.
+  const uint32_t nmine = blockIdx.x < a.nbins ? (a.nbins - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
+  for (uint32_t j = threadIdx.x; j < nmine; j += blockDim.x) {
+    const uint32_t bb = blockIdx.x + j * gridDim.x;
+    bl_start[j] = a.BS[bb];
+    bl_size[j] = a.T[bb];
+  }
+  __syncthreads();
+  auto skip = [&](uint32_t j) {
+    while (j < nmine && bl_size[j] > a.emax) ++j;
+    return j;
   };
-  auto issue = [&](uint32_t b, int buf) {
+  auto issue = [&](uint32_t j, int buf) {
     if (threadIdx.x == 0) {
-      const uint64_t k0 = a.BS[b], k1 = k0 + a.T[b];
+      const uint64_t k0 = bl_start[j], k1 = k0 + bl_size[j];
       const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(k0, k1);
       const TileSpan<4> si_ = tile_span<4>(k0, k1);
       mbar_arrive_expect_tx(&bar[buf], sk_.bytes() + si_.bytes());
@@ -444,36 +484,128 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map m
     mbar_fence_init();
   }
   __syncthreads();
-  uint32_t b = skip(blockIdx.x);
-  if (b >= a.nbins) return;
-  issue(b, 0);
-  for (uint32_t it = 0; b < a.nbins; ++it) {
-    const int buf = it & 1;
-    const uint32_t nb_next = skip(b + gridDim.x);
-    if (nb_next < a.nbins) issue(nb_next, buf ^ 1);
-    if (!mbar_wait_block(&bar[buf], (it >> 1) & 1u, a.status)) return;
-    const uint32_t E = a.T[b], start = a.BS[b];
+  uint32_t jb = skip(0);
+  if (jb >= nmine) return;
+  issue(jb, 0);
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  for (uint32_t it = 0; jb < nmine; ++it) {
+    const uint32_t b = blockIdx.x + jb * gridDim.x;
+    const int buf = nbuf == 2 ? (int)(it & 1) : 0;
+    const uint32_t jb_next = skip(jb + 1);
+    if (nbuf == 2 && jb_next < nmine) issue(jb_next, buf ^ 1);
+    const uint64_t bucket0 = (uint64_t)b << a.s;
+    const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
+    const uint32_t nwords = (nb + 1) >> 1;
+    for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) cnt[w] = 0;
+    if (threadIdx.x == 0) *nheavy = 0;
+    const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
+    if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
+    const uint32_t E = bl_size[jb], start = bl_start[jb];
     const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(start, (uint64_t)start + E);
     const TileSpan<4> si_ = tile_span<4>(start, (uint64_t)start + E);
     load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
     load_tail<4>(iin[buf], a.in_i, si_);
-    const uint64_t bucket0 = (uint64_t)b << a.s;
-    const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
-    __syncthreads();
+    if (sk_.a0 + sk_.body < (uint64_t)start + E || si_.a0 + si_.body < (uint64_t)start + E)
+      __syncthreads();  // tail elements came in by plain loads (block-uniform condition)
     const K* kk = kin[buf] + (start - sk_.a0);
     const uint32_t* ii = iin[buf] + (start - si_.a0);
-    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
-      lb[e] = (uint16_t)(map(kk[e]) - (uint32_t)bucket0);
+    // 1. local buckets and counts
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+      const uint32_t l = map(kk[e]) - (uint32_t)bucket0;
+      lb[e] = (uint16_t)l;
+      atomicAdd(&cnt[l >> 1], 1u << ((l & 1u) << 4));
+    }
     __syncthreads();
-    const uint16_t* sorted = sort_positions_by_bucket<IPT, NW, uint16_t>(lb, E, nb, tmp, perm, wc, wsum);
-    write_offsets_from_sorted(lb, sorted, E, nb, bucket0, start, a.offsets);
+    // 2. exclusive scan of the counts; offsets of the bin's buckets
+    {
+      const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
+      const uint32_t w0 = threadIdx.x * per, w1 = min(w0 + per, nwords);
+      uint32_t s = 0;
+      for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t x = cnt[w];
+        s += (x & 0xffffu) + (x >> 16);
+      }
+      uint32_t base = block_excl_scan_nt<uint32_t>(s, wsum);
+      for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
+        const uint32_t v = 2 * w;
+        a.offsets[bucket0 + v] = start + base;
+        if (v + 1 < nb) a.offsets[bucket0 + v + 1] = start + base + lo;
+        cnt[w] = base | ((base + lo) << 16);
+        base += lo + hi;
+      }
+    }
+    __syncthreads();
+    // 3. slots
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+      const uint32_t l = lb[e], sh = (l & 1u) << 4;
+      const uint32_t old = atomicAdd(&cnt[l >> 1], 1u << sh);
+      opos[(old >> sh) & 0xffffu] = (uint16_t)e;
+    }
+    __syncthreads();
+    // 4. order inside each bucket: ascending position
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
+      const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
+      const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
+      const uint32_t c = end - beg;
+      if (c < 2) continue;
+      if (c <= kBinSmallBucket) {
+        for (uint32_t i = beg + 1; i < end; ++i) {
+          const uint16_t p = opos[i];
+          uint32_t j = i;
+          while (j > beg && opos[j - 1] > p) {
+            opos[j] = opos[j - 1];
+            --j;
+          }
+          opos[j] = p;
+        }
+      } else {
+        heavy[atomicAdd(nheavy, 1u)] = (uint16_t)v;
+      }
+    }
+    __syncthreads();
+    const uint32_t nh = *nheavy;
+    if (nh > 0 && warp < kBinBitmapWarps) {
+      // lb is dead: each of the first kBinBitmapWarps warps owns emax bits of it
+      const uint32_t nbits_words = (E + 31) >> 5;
+      uint32_t* bm = (uint32_t*)lb + warp * (a.emax >> 5);
+      for (uint32_t h = warp; h < nh; h += kBinBitmapWarps) {
+        const uint32_t v = heavy[h];
+        const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
+        const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
+        for (uint32_t k = lane; k < nbits_words; k += 32) bm[k] = 0;
+        __syncwarp();
+        for (uint32_t i = beg + lane; i < end; i += 32) {
+          const uint32_t p = opos[i];
+          atomicOr(&bm[p >> 5], 1u << (p & 31u));
+        }
+        __syncwarp();
+        uint32_t run = beg;
+        for (uint32_t k0 = 0; k0 < nbits_words; k0 += 32) {
+          uint32_t word = k0 + lane < nbits_words ? bm[k0 + lane] : 0u;
+          const uint32_t c = __popc(word);
+          const uint32_t incl = warp_incl_scan(c);
+          uint32_t pos = run + incl - c;
+          while (word) {
+            const uint32_t bit = __ffs(word) - 1;
+            opos[pos++] = (uint16_t)(((k0 + lane) << 5) + bit);
+            word &= word - 1;
+          }
+          run += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+      }
+    }
+    if (nh > 0) __syncthreads();  // block-uniform: every thread read the same count
+    // 5. edges in bucket order
     for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
-      const uint32_t p = sorted[j];
+      const uint32_t p = opos[j];
       a.csr_k[start + j] = kk[p];
       a.csr_i[start + j] = ii[p];
     }
     __syncthreads();
-    b = nb_next;
+    if (nbuf == 1 && jb_next < nmine) issue(jb_next, 0);
+    jb = jb_next;
   }
 }
 
@@ -496,8 +628,8 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
   uint16_t* tmp = (uint16_t*)sp; sp += kBigTile * 2;
   uint16_t* perm = (uint16_t*)sp; sp += kBigTile * 2;
   uint16_t* slb = (uint16_t*)sp; sp += kBigTile * 2;
-  uint16_t* wc = (uint16_t*)sp; sp += 256 * NW * 2;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  uint32_t* wc = (uint32_t*)sp; sp += rank_words<NW>() * 4;
   uint32_t* wsum = (uint32_t*)sp;
   const uint32_t novf = *ovf_count;
   for (uint32_t k = blockIdx.x; k < novf; k += gridDim.x) {
@@ -525,7 +657,7 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
         lb[e] = (uint16_t)(map(key) - (uint32_t)bucket0);
       }
       __syncthreads();
-      const uint16_t* sorted = sort_positions_by_bucket<IPT, NW, uint16_t>(lb, cnt, nb, tmp, perm, wc, wsum);
+      const uint16_t* sorted = sort_positions_by_bucket<IPT, NW>(lb, cnt, nb, tmp, perm, wc, wsum);
       for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) slb[j] = lb[sorted[j]];
       __syncthreads();
       for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
@@ -627,7 +759,7 @@ __global__ void __launch_bounds__(kV1HeavyNW * 32) k_v1_fix_heavy(const uint32_t
   uint8_t* sp = smem;
   K* sk = (K*)sp; sp += TILE * sizeof(K);
   uint32_t* sv = (uint32_t*)sp; sp += TILE * 4;
-  uint32_t* wc = (uint32_t*)sp; sp += 256 * NW * 4;
+  uint32_t* wc = (uint32_t*)sp; sp += rank_words<NW>() * 4;
   uint32_t* dstart = (uint32_t*)sp; sp += 256 * 4;
   uint32_t* cursor = (uint32_t*)sp; sp += 256 * 4;
   uint8_t* sd = sp; sp += TILE;
@@ -753,8 +885,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.BS = BS;
   pa.status = status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr);
-    auto kern = k_partition<K, Map, false>;
+    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, kPartIPT, false);
+    auto kern = k_partition<K, Map, false, kPartIPT>;
     set_smem_once(kern, sm);
     {
       HG_TRACE("k_partition_A", st);
@@ -767,13 +899,18 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     pb.in_i = csr_i;
     pb.out_k = bk;
     pb.out_i = bi;
-    const size_t sm = part_smem_bytes(sizeof(K), true);
-    auto kern = k_partition<K, Map, true>;
+    const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true);
+    auto kern = k_partition<K, Map, true, kPartIPTB>;
     set_smem_once(kern, sm);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPartNW * 32, sm);
-    const uint64_t items = (uint64_t)p.nsb * p.G;
-    const unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)std::max(1, per_sm) * di.sms);
+    // ~32K edges per item: enough to amortise the per-item set-up
+    const uint64_t per_chunk_sb = std::max<uint64_t>(1, p.n / ((uint64_t)p.G * p.nsb));
+    pb.gg = (uint32_t)std::min<uint64_t>(p.G, std::max<uint64_t>(1, 32768 / per_chunk_sb));
+    pb.ngroups = (p.G + pb.gg - 1) / pb.gg;
+    const uint64_t items = (uint64_t)p.nsb * pb.ngroups;
+    unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)std::max(1, per_sm) * di.sms);
+    grid = (unsigned)std::max<uint64_t>(grid, (items + kMaxItemsPerCta - 1) / kMaxItemsPerCta);
     {
       HG_TRACE("k_partition_B", st);
       kern<<<grid, kPartNW * 32, sm, st>>>(pb, map);
@@ -793,11 +930,16 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   ba.emax = p.emax;
   ba.status = status;
   {
-    constexpr int IPT = bin_ipt<K>();
-    const size_t sm = bin_smem_bytes(sizeof(K), p.emax);
-    auto kern = k_binbuild<K, Map, IPT>;
+    size_t sm = bin_smem_bytes(sizeof(K), p.emax, p.s, 2);
+    ba.nbuf = 2;
+    if (sm > (size_t)di.max_smem_optin) {
+      sm = bin_smem_bytes(sizeof(K), p.emax, p.s, 1);
+      ba.nbuf = 1;
+    }
+    auto kern = k_binbuild<K, Map>;
     set_smem_once(kern, sm);
-    const unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms);
+    unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms);
+    grid = std::max<unsigned>(grid, (p.nbins + kMaxBinsPerCta - 1) / kMaxBinsPerCta);
     {
       HG_TRACE("k_binbuild", st);
       kern<<<grid, kBinNW * 32, sm, st>>>(ba, map);
@@ -857,8 +999,8 @@ hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, u
   uint32_t nbits = 8;
   while (nbits < 32 && (n - 1) >> nbits) nbits += 8;
   {
-    const size_t sm = align_up((size_t)kV1HeavyNW * 32 * kPartIPT * (sizeof(K) + 5) + 256 * kV1HeavyNW * 4 +
-                               2 * 256 * 4, 16) + 32 * 4 + 64;
+    const size_t sm = align_up((size_t)kV1HeavyNW * 32 * kPartIPT * (sizeof(K) + 5) +
+                               (size_t)rank_words<kV1HeavyNW>() * 4 + 2 * 256 * 4, 16) + 32 * 4 + 64;
     auto kern = k_v1_fix_heavy<K>;
     set_smem_once(kern, sm);
     {
@@ -874,12 +1016,192 @@ hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, u
   return last_launch_status();
 }
 
+// ===========================================================================
+// Binned probe.  HashGraph-Probe-Standard answers each query with random
+// reads into the table; on HBM every random 4-byte read costs a whole DRAM
+// burst.  Here the queries are first partitioned by bucket range into ng
+// groups (the build's histogram and stable partition kernels, applied to the
+// queries), so that the group being probed touches one table slice small
+// enough to stay in L2; the per-query counts are then put back in query
+// order by a merge over the groups (inside a group the query positions
+// ascend, because the partition is stable).
+// ===========================================================================
+constexpr int kUnpermuteThreads = 1024;
+constexpr uint32_t kUnpermuteTile = 8192;
+constexpr int kUnpermuteGPW = 8;  // groups per warp: 256 groups / 32 warps
+
+__global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t* __restrict__ Qi,
+                                                                 const uint32_t* __restrict__ Qc,
+                                                                 const uint32_t* __restrict__ GS, uint32_t ng,
+                                                                 uint64_t Q, uint64_t span,
+                                                                 uint32_t* __restrict__ counts) {
+  __shared__ uint32_t cur[256], gend[256];
+  __shared__ uint32_t out_s[kUnpermuteTile];
+  const uint64_t ob = (uint64_t)blockIdx.x * span;
+  if (ob >= Q) return;
+  const uint64_t oe = min(ob + span, Q);
+  if (threadIdx.x < ng) {  // first query of each group at or after ob
+    uint32_t lo = GS[threadIdx.x], hi = GS[threadIdx.x + 1];
+    gend[threadIdx.x] = hi;
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if (Qi[mid] < ob) lo = mid + 1; else hi = mid;
+    }
+    cur[threadIdx.x] = lo;
+  }
+  __syncthreads();
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t o0 = ob; o0 < oe; o0 += kUnpermuteTile) {
+    const uint64_t o1 = min(o0 + (uint64_t)kUnpermuteTile, oe);
+    uint32_t c[kUnpermuteGPW], e[kUnpermuteGPW];
+    bool act[kUnpermuteGPW];
+#pragma unroll
+    for (int k = 0; k < kUnpermuteGPW; ++k) {
+      const uint32_t g = warp + k * nw;
+      act[k] = g < ng;
+      c[k] = act[k] ? cur[g] : 0u;
+      e[k] = act[k] ? gend[g] : 0u;
+    }
+    bool any = true;
+    while (any) {
+      uint32_t v[kUnpermuteGPW], x[kUnpermuteGPW];
+#pragma unroll
+      for (int k = 0; k < kUnpermuteGPW; ++k) {
+        v[k] = 0xffffffffu;
+        x[k] = 0u;
+        const uint32_t j = c[k] + lane;
+        if (act[k] && j < e[k]) {
+          v[k] = __ldcs(Qi + j);
+          x[k] = __ldcs(Qc + j);
+        }
+      }
+      any = false;
+#pragma unroll
+      for (int k = 0; k < kUnpermuteGPW; ++k) {
+        if (!act[k]) continue;  // warp-uniform
+        const bool in = (uint64_t)v[k] < o1;
+        if (in) out_s[v[k] - (uint32_t)o0] = x[k];
+        const uint32_t n = __popc(__ballot_sync(kFull, in));
+        c[k] += n;
+        act[k] = n == 32;
+        any |= act[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kUnpermuteGPW; ++k) {
+      const uint32_t g = warp + k * nw;
+      if (g < ng && lane == 0) cur[g] = c[k];
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < (uint32_t)(o1 - o0); t += blockDim.x) __stcs(counts + o0 + t, out_s[t]);
+    __syncthreads();
+  }
+}
+
+bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePlan* p) {
+  const DevInfo& di = dev_info();
+  const int kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  const uint64_t V = cfg->num_buckets;
+  const double table_bytes = 4.0 * (double)(V + 1) + (double)kb * (double)table_n;
+  int lng = 0;
+  while (lng < 8 && table_bytes / (double)(1u << lng) > (double)kProbeSliceBytes) ++lng;
+  int sg = ceil_log2_u64(V) - lng;
+  if (sg < 0) sg = 0;
+  p->sg = (uint32_t)sg;
+  p->ng = (uint32_t)(((V - 1) >> sg) + 1);
+  if (p->ng > 256) return false;
+  const int sms = std::max(di.sms, 1);
+  uint64_t chunk = std::max<uint64_t>(kPartTile, (q + 2 * sms - 1) / (2 * sms));
+  chunk = (chunk + 15) / 16 * 16;
+  p->chunk = chunk;
+  p->G = (uint32_t)std::max<uint64_t>(1, (q + chunk - 1) / chunk);
+  size_t o = sizeof(WsHeader);
+  p->o_H = o;   o = align_up(o + (size_t)p->G * p->ng * 4);
+  p->o_C = o;   o = align_up(o + (size_t)p->G * p->ng * 4);
+  p->o_CT = o;  o = align_up(o + (size_t)p->ng * 4);
+  p->o_GS = o;  o = align_up(o + ((size_t)p->ng + 1) * 4);
+  p->o_ovf = o; o = align_up(o + (size_t)p->ng * 4 + 16);
+  p->o_qk = o;  o = align_up(o + ((size_t)q + 16) * kb);
+  p->o_qi = o;  o = align_up(o + ((size_t)q + 16) * 4);
+  p->o_qc = o;  o = align_up(o + ((size_t)q + 16) * 4);
+  p->total = o;
+  return true;
+}
+
+template <typename K, typename Map>
+hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, const K* queries, uint64_t q,
+                            uint32_t* counts, uint8_t* ws, cudaStream_t st, Map map) {
+  WsHeader* hdr = (WsHeader*)ws;
+  uint32_t* H = (uint32_t*)(ws + p.o_H);
+  uint32_t* C = (uint32_t*)(ws + p.o_C);
+  uint32_t* CT = (uint32_t*)(ws + p.o_CT);
+  uint32_t* GS = (uint32_t*)(ws + p.o_GS);
+  uint32_t* ovf = (uint32_t*)(ws + p.o_ovf);
+  K* qk = (K*)(ws + p.o_qk);
+  uint32_t* qi = (uint32_t*)(ws + p.o_qi);
+  uint32_t* qc = (uint32_t*)(ws + p.o_qc);
+  const DevInfo& di = dev_info();
+  {
+    const size_t sm = (size_t)p.ng * 4;
+    auto kern = k_hist<K, Map>;
+    set_smem_once(kern, std::max<size_t>(sm, 1024));
+    HG_TRACE("k_hist_Q", st);
+    kern<<<p.G, kHistThreads, std::max<size_t>(sm, 1024), st>>>(queries, q, p.chunk, p.sg, p.ng, 0, p.ng, H, C, map);
+  }
+  {
+    HG_TRACE("k_colscan_Q", st);
+    k_colscan<<<(p.ng + 255) / 256, 256, 0, st>>>(C, p.G, p.ng, CT);
+  }
+  {
+    HG_TRACE("k_scan_Q", st);
+    // no bin is "oversized" here; the closing-offset store goes to scratch
+    k_scan_bins<<<1, 1024, 0, st>>>(CT, p.ng, GS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.ng, 0,
+                                    (uint32_t)q);
+  }
+  PartArgs<K> pa{};
+  pa.in_k = queries;
+  pa.in_i = nullptr;  // ids = query positions
+  pa.out_k = qk;
+  pa.out_i = qi;
+  pa.n = q;
+  pa.chunk = p.chunk;
+  pa.G = p.G;
+  pa.s = p.sg;
+  pa.sshift = 0;
+  pa.nbins = p.ng;
+  pa.nsb = p.ng;
+  pa.H = H;
+  pa.C = C;
+  pa.CT = CT;
+  pa.BS = GS;
+  pa.status = &hdr->status;
+  {
+    const size_t sm = part_smem_bytes(sizeof(K), false, kPartIPT, false);
+    auto kern = k_partition<K, Map, false, kPartIPT>;
+    set_smem_once(kern, sm);
+    HG_TRACE("k_partition_Q", st);
+    kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
+  }
+  hg_status rc = probe_launch<K, Map>(qk, q, t->d_offsets, (const K*)t->d_keys, qc, V, st, map);
+  if (rc != HG_OK) return rc;
+  {
+    const uint64_t tiles = (q + kUnpermuteTile - 1) / kUnpermuteTile;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)2 * di.sms));
+    const uint64_t span = (q + grid - 1) / grid;
+    HG_TRACE("k_unpermute", st);
+    k_unpermute<<<(unsigned)grid, kUnpermuteThreads, 0, st>>>(qi, qc, GS, p.ng, q, span, counts);
+  }
+  return last_launch_status();
+}
+
 // Explicit instantiations used by hg_api.cu (build entry point).
 #define HG_INST(K, M)                                                                                   \
   template hg_status build_v2<K, M>(const Plan&, const K*, const uint32_t*, uint32_t*, K*, uint32_t*, \
                                     uint8_t*, cudaStream_t, M);                                         \
   template hg_status build_v1<K, M>(uint64_t, uint64_t, const K*, const uint32_t*, uint32_t*, K*,       \
-                                    uint32_t*, uint8_t*, cudaStream_t, M);
+                                    uint32_t*, uint8_t*, cudaStream_t, M);                              \
+  template hg_status probe_binned_impl<K, M>(const ProbePlan&, uint64_t, const hg_table*, const K*,     \
+                                             uint64_t, uint32_t*, uint8_t*, cudaStream_t, M);
 HG_INST(uint32_t, MurmurMap)
 HG_INST(uint64_t, MurmurMap)
 HG_INST(uint32_t, LearnedMap)

@@ -8,11 +8,35 @@ namespace hg {
 constexpr int kHistThreads = 1024;
 constexpr uint32_t kMaxBinsLog2 = 15;  // bins counted in one shared-memory histogram
 constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local index, 128 KB cursors)
-constexpr int kPartNW = 16;            // warps of the partition kernels
-constexpr int kPartIPT = 8;            // items per thread
+// Partition geometry (compile-time; the defaults are the tuned values).
+#ifndef HG_PART_NW
+#define HG_PART_NW 16
+#endif
+#ifndef HG_PART_IPT
+#define HG_PART_IPT 8
+#endif
+#ifndef HG_PART_IPTB
+#define HG_PART_IPTB 6
+#endif
+#ifndef HG_PART_MINB
+#define HG_PART_MINB 2
+#endif
+constexpr int kPartNW = HG_PART_NW;      // warps of the partition kernels
+constexpr int kPartIPT = HG_PART_IPT;    // items per thread, pass A
+constexpr int kPartIPTB = HG_PART_IPTB;  // items per thread, pass B (smaller tile: 2 CTAs per SM)
+constexpr int kPartMinBlocks = HG_PART_MINB;
+constexpr uint32_t kMaxItemsPerCta = 128;  // pass B work items one CTA may own
+constexpr uint32_t kMaxBinsPerCta = 256;   // bins one bin-build CTA may own
 constexpr int kPartTile = kPartNW * 32 * kPartIPT;  // 4096 elements per tile
-constexpr int kBinNW = 32;             // warps of the bin-build kernels (1024 threads)
-constexpr int kBigTile = 4096;         // tile of the oversized-bin kernel
+#ifndef HG_BIN_NW
+#define HG_BIN_NW 32
+#endif
+constexpr int kBinNW = HG_BIN_NW;      // warps of the bin-build kernels (1024 threads)
+constexpr int kBigTile = 2048;         // tile of the oversized-bin kernel
+constexpr uint32_t kBinEmaxU32 = 10240; // largest bin built in shared memory (uint32 keys)
+constexpr uint32_t kBinEmaxU64 = 7168;  // same for uint64 keys
+constexpr uint32_t kBinSmallBucket = 32; // bucket length sorted by one thread in the bin build
+constexpr uint32_t kBinBitmapWarps = 16; // warps sorting longer buckets with position bitmaps
 constexpr uint32_t kV1Small = 32;      // V1 fix-up: longest bucket sorted by one thread
 constexpr int kV1HeavyNW = 16;
 
@@ -30,6 +54,20 @@ struct Plan {
 };
 
 bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p);
+
+// Binned probe: query groups by bucket range, workspace layout.
+constexpr double kProbeSliceBytes = 16.0 * 1024 * 1024;  // table bytes per query group (L2-resident)
+struct ProbePlan {
+  uint32_t sg;   // group = bucket >> sg
+  uint32_t ng;   // groups (<= 256)
+  uint32_t G;    // query chunks
+  uint64_t chunk;
+  size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, total;
+};
+bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePlan* p);
+template <typename K, typename Map>
+hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, const K* queries, uint64_t q,
+                            uint32_t* counts, uint8_t* ws, cudaStream_t st, Map map);
 size_t v1_workspace_bytes(int kb, uint64_t n, uint64_t V);
 
 template <typename K, typename Map>

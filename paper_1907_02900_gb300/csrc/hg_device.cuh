@@ -203,6 +203,23 @@ __device__ __forceinline__ T block_excl_scan(T v, T* wsum, T* total) {
   return base;
 }
 
+// Exclusive block scan without the trailing barrier: wsum may be reused only
+// after the caller's next __syncthreads.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan_nt(T v, T* wsum) {
+  const int lane = lane_id(), w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  T incl = warp_incl_scan(v);
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    T x = lane < nw ? wsum[lane] : T(0);
+    x = warp_incl_scan(x);
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  return (w ? wsum[w - 1] : T(0)) + incl - v;
+}
+
 // In-place exclusive scan of a[0..m) in shared memory by the whole block
 // (sums carried in 32 bits).  Returns the total.  wsum: smem u32[32].
 template <typename T>
@@ -232,22 +249,33 @@ __device__ __forceinline__ uint32_t block_excl_scan_smem(T* a, int m, uint32_t* 
 // holds element w*32*IPT + r*32 + l.  Inside a warp, equal digits of one
 // round are grouped with __match_any_sync and ranked by lane; a per-(digit,
 // warp) counter carries the running count from round to round, so ranks
-// follow the sequence order.  An exclusive scan of the counters in
-// digit-major, warp-minor order then gives every (digit, warp) its base in
-// the stably sorted sequence.
+// follow the sequence order.  Then each digit's thread turns its row of
+// warp counters into an exclusive prefix, a block scan over the digit totals
+// gives every digit its start, and (digit start + warp prefix + rank in
+// warp) is the element's position in the stably sorted sequence.
+// Counters live at wc[d*(NW+1) + w]: the odd row stride puts the leaders of
+// different digits, and the threads of different digits, in different
+// shared-memory banks; slot NW of each row receives the digit's start.
 //   dig[r]   digit of the element held in round r (ignored when invalid)
 //   dest[r]  out: position of that element in the stably sorted sequence
-//   wc       smem CT[ndig*NW] (scratch; CT = uint16_t when n < 65536)
+//   wc       smem u32[ndig*(NW+1)] (scratch)
 //   dstart   smem u32[ndig] out: first sorted position of each digit (or null)
 //   wsum     smem u32[32] (scratch)
-// Contains __syncthreads; every thread of the block must call it.
+// Requires ndig <= blockDim.x.  Contains __syncthreads; every thread of the
+// block must call it.
 // ---------------------------------------------------------------------------
-template <int IPT, int NW, typename CT>
+template <int NW>
+__host__ __device__ constexpr int rank_row() {
+  return NW + 1 + (NW & 1);  // odd row stride with a spare slot after the NW counters
+}
+
+template <int IPT, int NW>
 __device__ __forceinline__ void block_stable_rank(const uint32_t (&dig)[IPT], uint32_t n,
-                                                  uint32_t (&dest)[IPT], int ndig, CT* wc,
+                                                  uint32_t (&dest)[IPT], int ndig, uint32_t* wc,
                                                   uint32_t* dstart, uint32_t* wsum) {
+  constexpr int S = rank_row<NW>();
   const int lane = lane_id(), w = threadIdx.x >> 5;
-  const int m = ndig * NW;
+  const int m = ndig * S;
   for (int i = threadIdx.x; i < m; i += blockDim.x) wc[i] = 0;
   __syncthreads();
   const uint32_t seg0 = (uint32_t)w * (32u * IPT);
@@ -262,8 +290,8 @@ __device__ __forceinline__ void block_stable_rank(const uint32_t (&dig)[IPT], ui
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
       if (valid && lane == leader) {
-        old = (uint32_t)wc[d * NW + w];
-        wc[d * NW + w] = (CT)(old + __popc(peers));
+        old = wc[d * S + w];
+        wc[d * S + w] = old + __popc(peers);
       }
       old = __shfl_sync(kFull, old, leader);
       dest[r] = old + __popc(peers & lt);
@@ -273,13 +301,28 @@ __device__ __forceinline__ void block_stable_rank(const uint32_t (&dig)[IPT], ui
     }
   }
   __syncthreads();
-  block_excl_scan_smem(wc, m, wsum);
-  if (dstart)
-    for (int d = threadIdx.x; d < ndig; d += blockDim.x) dstart[d] = (uint32_t)wc[d * NW];
+  uint32_t tot = 0;
+  const int t = threadIdx.x;
+  if (t < ndig) {
+    uint32_t c[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) c[k] = wc[t * S + k];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      wc[t * S + k] = tot;
+      tot += c[k];
+    }
+  }
+  const uint32_t start = block_excl_scan<uint32_t>(tot, wsum, (uint32_t*)nullptr);
+  if (t < ndig) {
+    wc[t * S + NW] = start;
+    if (dstart) dstart[t] = start;
+  }
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
-    if (idx < n) dest[r] += (uint32_t)wc[dig[r] * NW + w];
+    if (idx < n) dest[r] += wc[dig[r] * S + NW] + wc[dig[r] * S + w];
   }
   __syncthreads();
 }

@@ -1,10 +1,16 @@
-// Tile-level stable partition and in-shared-memory counting sort, shared by
-// the build, the overflow path and the V1 fix-up.
+// Tile-level stable partition and in-shared-memory counting sorts, shared by
+// the build, the oversized-bin path and the V1 fix-up.
 #pragma once
 
 #include "hg_device.cuh"
 
 namespace hg {
+
+// Shared-memory words of block_stable_rank's counter matrix for 256 digits.
+template <int NW>
+__host__ __device__ constexpr int rank_words() {
+  return 256 * rank_row<NW>();
+}
 
 // Stable partition of one tile (held in registers, IPT items per thread in
 // block_stable_rank order) into global memory through running per-digit
@@ -20,7 +26,7 @@ __device__ __forceinline__ void tile_partition_out(const K (&key)[IPT], const ui
                                                    uint32_t* wsum, K* __restrict__ out_k,
                                                    uint32_t* __restrict__ out_v) {
   uint32_t dest[IPT];
-  block_stable_rank<IPT, NW, uint32_t>(dig, n, dest, ndig, wc, dstart, wsum);
+  block_stable_rank<IPT, NW>(dig, n, dest, ndig, wc, dstart, wsum);
   const uint32_t seg0 = (threadIdx.x >> 5) * (32u * IPT), lane = lane_id();
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
@@ -46,23 +52,106 @@ __device__ __forceinline__ void tile_partition_out(const K (&key)[IPT], const ui
   __syncthreads();
 }
 
+// The same stable tile partition with fewer barriers (six per tile):
+// per-digit output bases are computed once as delta[d] = cursor[d] - start[d]
+// while the cursors advance in the same step, and the counter matrix is
+// cleared after its last read, so it is already zero for the next tile.
+// Preconditions: wc[0 .. 256*rank_row<NW>()) is zero; ndig <= blockDim.x.
+template <typename K, int IPT, int NW>
+__device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const uint32_t (&val)[IPT],
+                                                    const uint32_t (&dig)[IPT], uint32_t n, int ndig, K* sk,
+                                                    uint32_t* sv, uint8_t* sd, uint32_t* wc, uint32_t* delta,
+                                                    uint32_t* cursor, uint32_t* wsum, K* __restrict__ out_k,
+                                                    uint32_t* __restrict__ out_v) {
+  constexpr int S = rank_row<NW>();
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const uint32_t seg0 = (uint32_t)w * (32u * IPT);
+  const uint32_t lt = lanemask_lt();
+  // Ranks inside each round come from __match_any_sync; the round's leader
+  // carries the warp's running count of the digit (plain shared-memory
+  // read-modify-write, ordered from round to round by __syncwarp).
+  uint32_t rank[IPT];
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+    rank[r] = 0;
+    if (seg0 + (uint32_t)r * 32u < n) {  // warp-uniform
+      const bool valid = idx < n;
+      const uint32_t d = valid ? dig[r] : (0x10000u + lane);
+      const uint32_t peers = __match_any_sync(kFull, d);
+      const int leader = __ffs(peers) - 1;
+      uint32_t old = 0;
+      if (valid && lane == leader) {
+        old = wc[d * S + w];
+        wc[d * S + w] = old + __popc(peers);
+      }
+      old = __shfl_sync(kFull, old, leader);
+      rank[r] = old + __popc(peers & lt);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  uint32_t tot = 0;
+  if (t < ndig) {
+    uint32_t c[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) c[k] = wc[t * S + k];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      wc[t * S + k] = tot;
+      tot += c[k];
+    }
+  }
+  const uint32_t start = block_excl_scan_nt<uint32_t>(tot, wsum);
+  if (t < ndig) {
+    wc[t * S + NW] = start;
+    delta[t] = cursor[t] - start;
+    cursor[t] += tot;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+    if (idx < n) {
+      const uint32_t d = dig[r];
+      const uint32_t dest = wc[d * S + NW] + wc[d * S + w] + rank[r];
+      sk[dest] = key[r];
+      sv[dest] = val[r];
+      sd[dest] = (uint8_t)d;
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const uint32_t g = delta[sd[j]] + j;
+    out_k[g] = sk[j];
+    out_v[g] = sv[j];
+  }
+  for (int i = threadIdx.x; i < ndig * S; i += blockDim.x) wc[i] = 0;
+  __syncthreads();
+}
+
 // Stable counting sort of tile positions 0..n-1 by a local bucket index
-// lb[p] < nb (nb <= 65536), by two least-significant-digit passes of 8 bits
-// (one pass when nb <= 256).  Returns the array holding the sorted
-// positions (tmp or perm).  wc: smem CT[256*NW].
-template <int IPT, int NW, typename CT>
+// lb[p] < nb (nb <= 65536), by two least-significant-digit passes that split
+// the index bits evenly (one pass when nb <= 256).  Returns the array
+// holding the sorted positions (tmp or perm).  wc: smem u32[rank_words<NW>()].
+template <int IPT, int NW>
 __device__ __forceinline__ const uint16_t* sort_positions_by_bucket(const uint16_t* lb, uint32_t n,
                                                                     uint32_t nb, uint16_t* tmp,
-                                                                    uint16_t* perm, CT* wc,
+                                                                    uint16_t* perm, uint32_t* wc,
                                                                     uint32_t* wsum) {
   const uint32_t seg0 = (threadIdx.x >> 5) * (32u * IPT), lane = lane_id();
+  uint32_t bits = 0;
+  while ((1u << bits) < nb) ++bits;
+  const uint32_t lo_bits = nb <= 256 ? bits : (bits + 1) / 2;
+  const uint32_t lo_mask = (1u << lo_bits) - 1u;
   uint32_t d[IPT], dest[IPT];
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
-    d[r] = idx < n ? (uint32_t)(lb[idx] & 255u) : 0u;
+    d[r] = idx < n ? ((uint32_t)lb[idx] & lo_mask) : 0u;
   }
-  block_stable_rank<IPT, NW, CT>(d, n, dest, nb < 256 ? (int)nb : 256, wc, (uint32_t*)nullptr, wsum);
+  block_stable_rank<IPT, NW>(d, n, dest, nb <= 256 ? (int)nb : (int)(1u << lo_bits), wc, (uint32_t*)nullptr, wsum);
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
@@ -75,9 +164,9 @@ __device__ __forceinline__ const uint16_t* sort_positions_by_bucket(const uint16
   for (int r = 0; r < IPT; ++r) {
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
     p[r] = idx < n ? tmp[idx] : 0u;
-    d[r] = idx < n ? (uint32_t)(lb[p[r]] >> 8) : 0u;
+    d[r] = idx < n ? ((uint32_t)lb[p[r]] >> lo_bits) : 0u;
   }
-  block_stable_rank<IPT, NW, CT>(d, n, dest, (int)((nb + 255) >> 8), wc, (uint32_t*)nullptr, wsum);
+  block_stable_rank<IPT, NW>(d, n, dest, (int)(((nb - 1) >> lo_bits) + 1), wc, (uint32_t*)nullptr, wsum);
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
@@ -85,22 +174,6 @@ __device__ __forceinline__ const uint16_t* sort_positions_by_bucket(const uint16
   }
   __syncthreads();
   return perm;
-}
-
-// CSR offsets of one bucket range from the sorted bucket sequence: bucket v
-// (local) starts at the number of elements whose bucket is below v.  The
-// thread handling sorted element j writes the offsets of every bucket in
-// (bucket(j-1), bucket(j)]; j == n closes the range.
-__device__ __forceinline__ void write_offsets_from_sorted(const uint16_t* lb, const uint16_t* sorted,
-                                                          uint32_t n, uint32_t nb, uint64_t bucket0,
-                                                          uint32_t start,
-                                                          uint32_t* __restrict__ offsets) {
-  for (uint32_t j = threadIdx.x; j <= n; j += blockDim.x) {
-    const int64_t cur = j < n ? (int64_t)lb[sorted[j]] : (int64_t)nb;
-    const int64_t prev = j > 0 ? (int64_t)lb[sorted[j - 1]] : -1;
-    const int64_t hi = cur < (int64_t)nb - 1 ? cur : (int64_t)nb - 1;
-    for (int64_t v = prev + 1; v <= hi; ++v) offsets[bucket0 + (uint64_t)v] = start + j;
-  }
 }
 
 }  // namespace hg

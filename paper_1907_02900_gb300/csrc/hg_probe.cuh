@@ -12,6 +12,6 @@ constexpr int kProbeQPT = 4;
 
 template <typename K, typename Map>
 hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck, uint32_t* out,
-                       cudaStream_t st, Map map);
+                       uint64_t V, cudaStream_t st, Map map);
 
 }  // namespace hg

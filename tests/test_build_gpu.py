@@ -95,6 +95,31 @@ def test_probe_u64_long_buckets(hg, orc):
     assert np.array_equal(to_np(hg.probe(t, to_dev(q))), orc.multiplicity(keys, q))
 
 
+@pytest.mark.parametrize("kt,nq,V,hit", [("u32", 300_001, 1 << 18, 0.5), ("u32", 1 << 20, 1 << 20, 1.0),
+                                          ("u32", 50_000, 1000, 0.3), ("u64", 400_000, 1 << 19, 0.5),
+                                          ("u32", 2_000_000, 3_000_017, 0.5), ("u32", 7, 1, 1.0)])
+def test_probe_binned_matches_oracle(hg, orc, kt, nq, V, hit):
+    # The binned probe returns exactly HashGraph-Probe-Standard's counts.
+    if kt == "u32":
+        keys = dg.dup_keys_u32(max(nq // 2, 1), 2, 31)
+        q = dg.queries_u32(nq, keys, hit, 32)
+    else:
+        keys = dg.zipf_keys_u64(nq // 2, 20_000, 31)
+        q = dg.queries_u64(nq, keys, hit, 32)
+    t = hg.build(to_dev(keys), V, seed=9)
+    got = to_np(hg.probe(t, to_dev(q), binned=True))
+    std = to_np(hg.probe(t, to_dev(q), binned=False))
+    assert np.array_equal(got, std)
+    assert np.array_equal(got, orc.multiplicity(keys, q))
+
+
+def test_probe_binned_empty_table(hg):
+    import torch
+    e = hg.build(torch.empty(0, dtype=torch.uint32, device="cuda"), 1 << 12)
+    q = to_dev(dg.uniform_keys_u32(100_000, 2))
+    assert np.all(to_np(hg.probe(e, q, binned=True)) == 0)
+
+
 def test_probe_empty_queries_and_table(hg):
     import torch
     t = hg.build(to_dev(dg.uniform_keys_u32(1000, 1)), 64)
@@ -123,7 +148,10 @@ def test_full_size_build_and_probe_sampled(hg, orc):
         s, e = int(off[v]), int(off[v + 1])
         assert np.array_equal(to_np(ck[s:e]), rk) and np.array_equal(to_np(ci[s:e]), ri)
     q = dg.queries_u32(1 << 28, keys, 0.5, dg.SEED_SCALE + 1)
-    counts = to_np(hg.probe(t, to_dev(q)))
+    dq = to_dev(q)
+    counts = to_np(hg.probe(t, dq, binned=True))
+    assert np.array_equal(counts, to_np(hg.probe(t, dq, binned=False)))
+    del dq
     qi = rng.integers(0, len(q), 20000)
     qs = q[qi]
     qb = orc.buckets(qs, V)
