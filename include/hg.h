@@ -142,6 +142,57 @@ hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_
                               int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
                               int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream);
 
+/* -------------------------------------------------------------- learned --
+ * Learned bucket map: an order-preserving stand-in for "hash(a) mod V".  It
+ * is not in the paper (Section 2 hashes with Murmur); the murmur map remains
+ * the default and the reference it is judged against.  Model (blob of
+ * hg_learned_model_bytes(L) bytes, 8-byte aligned):
+ *   header 32 B: u32 magic 'HGLM', u32 L, u64 V, f32 a, f32 b, u32 key_type, u32 flags
+ *   leaf   24 B: u64 xmin, f32 slope, f32 icpt, u32 base, u32 width
+ *   root:  leaf = clamp(floor(a * f(key) + b), 0, L-1), f(key) = fp32 of the
+ *          IEEE bits of fp32(key) (monotone, roughly 2^23 log2 key)
+ *   leaf j: bucket = base + clamp(floor(slope * fp32(key - xmin) + icpt), 0, width-1)
+ *   (fp32 round-to-nearest, no fused multiply-add; bucket < V; monotone in key)
+ * hg_learned_train draws a sample of sample_size keys (SplitMix64 indices,
+ * stream 'LEARN', seed), sorts it, fits the root, finds the knots
+ * (xmin_j = smallest key the root sends to leaf j or beyond), and fits the
+ * knot values of the continuous piecewise-linear CDF.  The prior Y0 is the
+ * interpolant, linear in the key, of the sample's rank targets
+ * (0, 0), (x_i, V(2i+1)/(2S)), (key max + 1, V) at the knots.  Then `iters`
+ * rounds of a Jacobi-preconditioned gradient step (step 0.9) on
+ *   loss(Y) = (1/S) [ sum_i (P(x_i) - V(2i+1)/(2S))^2 + rho sum_{j=1..J} (Y_j - Y0_j)^2 ]
+ * each followed by the projection onto
+ *   Y_j - Y_{j-1} >= gamma (Y0_j - Y0_{j-1})   (running max of Y - gamma Y0)
+ * with J the last leaf the root can reach, rho = 1 and gamma = 0.5: the
+ * ridge keeps the minimiser unique where knots see few samples, the floor
+ * keeps every leaf at least half as wide in buckets as the prior makes it.
+ * Deterministic.
+ *   d_diag (optional, L+5 doubles): [loss before, loss after, root loss,
+ *   unused, knot values Y_0..Y_L]
+ * hg_learned_sorted_sample / _root_grad / _leaf_grad expose the sampling and
+ * the gradients (root: loss, dL/da, dL/db in double; leaves: dL/dY_j and
+ * d2L/dY_j^2 in fp32 at knot values d_Y, Y0 taken from d_sorted) for
+ * checking.
+ * hg_bucket_stats: bucket-length max, mean, variance and non-empty count of a
+ * map over a key set (d_counts: V uint32 scratch). */
+size_t hg_learned_model_bytes(uint32_t num_leaves);
+size_t hg_learned_workspace_size(int32_t key_type, uint64_t n, uint64_t sample_size, uint32_t num_leaves);
+hg_status hg_learned_train(int32_t key_type, const void* d_keys, uint64_t n, uint64_t num_buckets,
+                           uint32_t num_leaves, uint64_t sample_size, uint64_t seed, uint32_t iters,
+                           void* d_model, double* d_diag, void* d_ws, size_t ws_bytes, void* stream);
+hg_status hg_learned_sorted_sample(int32_t key_type, const void* d_keys, uint64_t n,
+                                   uint64_t sample_size, uint64_t seed, uint64_t* d_out, void* d_ws,
+                                   size_t ws_bytes, void* stream);
+hg_status hg_learned_root_grad(int32_t key_type, const uint64_t* d_sorted, uint64_t S,
+                               uint32_t num_leaves, double a, double b, double* d_out3, void* d_ws,
+                               size_t ws_bytes, void* stream);
+hg_status hg_learned_leaf_grad(int32_t key_type, const uint64_t* d_sorted, uint64_t S,
+                               uint64_t num_buckets, float a, float b, uint32_t num_leaves,
+                               const double* d_Y, float* d_grad, float* d_diag, double* d_loss,
+                               void* d_ws, size_t ws_bytes, void* stream);
+hg_status hg_bucket_stats(const hg_config* cfg, const void* d_keys, uint64_t n, uint32_t* d_counts,
+                          double* d_out4, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------ build, no allocation --
  * The paper has no counterpart of this entry point.  It is hg_build (V2)
  * for callers that cannot allocate device memory -- code running inside a

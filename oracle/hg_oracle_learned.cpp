@@ -10,14 +10,26 @@
 //   spline: the bucket position of x in leaf j is
 //           Y_j + (Y_{j+1} - Y_j) * (x - kb_j) / (kb_{j+1} - kb_j),
 //           with knot values Y_0 = 0 <= Y_1 <= ... <= Y_L = V
-// Training fits the knot values to the empirical CDF of a key sample:
-//   loss(Y) = (1/S) sum_i (P(x_i) - V (2i+1) / (2S))^2   over the sorted sample
+// Prior: the knot values Y0 of the piecewise-linear interpolant of the
+// sample's rank targets, through (0, 0), (x_i, V (2i+1) / (2S)) for the
+// sorted sample x_0..x_{S-1}, and (key max + 1, V).
+// Training fits the knot values to the sample's rank targets:
+//   loss(Y) = (1/S) [ sum_i (P(x_i) - V (2i+1) / (2S))^2
+//                     + rho * sum_{j=1..J} (Y_j - Y0_j)^2 ]
+// by Jacobi-preconditioned gradient steps, each followed by the projection
+// onto the knot values that keep every leaf at least gamma times as wide (in
+// buckets) as the prior makes it:  Y_j - Y_{j-1} >= gamma (Y0_j - Y0_{j-1}).
+// The ridge rho makes the minimiser unique where knots see few samples; the
+// width floor keeps leaves that the sample barely sees from collapsing onto
+// one bucket.
 // This file computes, in double precision and in the plainest way:
 //   * the sample indices (SplitMix64, counter-based, as published by Steele,
 //     Lea and Flood 2014) and the sorted sample,
 //   * the knots of a given root by bisection on the exact fp32 root,
 //   * the loss, its gradient and the diagonal of its Hessian,
-//   * the exact least-squares knot values (tridiagonal normal equations),
+//   * the prior, the training iteration with its projection,
+//   * the exact least-squares knot values without the projection
+//     (tridiagonal normal equations),
 //   * the root least-squares fit and its gradient.
 #include <algorithm>
 #include <cmath>
@@ -119,10 +131,11 @@ static void leaf_coords(int key_type, const uint64_t* x, uint64_t S, float a, fl
 }
 
 // Loss, gradient dL/dY_j and Hessian diagonal d2L/dY_j^2 of the spline fit
-// (Y has L+1 entries; all L+1 partials are returned, fixed knots included).
+// (Y has L+1 entries; all L+1 partials are returned; the ridge term applies
+// to the free knots 1..J).
 double orc_rmi_leaf_loss_grad(int key_type, const uint64_t* x, uint64_t S, uint64_t V, float a, float b,
-                              uint32_t L, const uint64_t* kb, uint32_t J, const double* Y, double* grad,
-                              double* diag) {
+                              uint32_t L, const uint64_t* kb, uint32_t J, const double* Y, const double* Y0,
+                              double rho, double* grad, double* diag) {
   std::vector<uint32_t> leaf;
   std::vector<double> lam;
   leaf_coords(key_type, x, S, a, b, L, kb, J, leaf, lam);
@@ -140,6 +153,12 @@ double orc_rmi_leaf_loss_grad(int key_type, const uint64_t* x, uint64_t S, uint6
     diag[j] += 2.0 * (1.0 - l) * (1.0 - l);
     diag[j + 1] += 2.0 * l * l;
   }
+  for (uint32_t j = 1; j <= J; ++j) {
+    const double d = Y[j] - Y0[j];
+    loss += rho * d * d;
+    grad[j] += 2.0 * rho * d;
+    diag[j] += 2.0 * rho;
+  }
   for (uint32_t j = 0; j <= L; ++j) {
     grad[j] /= (double)S;
     diag[j] /= (double)S;
@@ -149,10 +168,10 @@ double orc_rmi_leaf_loss_grad(int key_type, const uint64_t* x, uint64_t S, uint6
 
 // Exact minimiser of the loss over the free knots Y_1..Y_J, with Y_0 = 0 and
 // Y_j = V for j > J: the normal equations are tridiagonal (each sample
-// touches two knots).  Free knots that no sample touches keep Y_init.
+// touches two knots) and, with rho > 0, strictly positive definite.
 // Thomas algorithm in double.
 void orc_rmi_leaf_lsq(int key_type, const uint64_t* x, uint64_t S, uint64_t V, float a, float b, uint32_t L,
-                      const uint64_t* kb, uint32_t J, const double* Y_init, double* Y_out) {
+                      const uint64_t* kb, uint32_t J, const double* Y_init, double rho, double* Y_out) {
   std::vector<uint32_t> leaf;
   std::vector<double> lam;
   leaf_coords(key_type, x, S, a, b, L, kb, J, leaf, lam);
@@ -170,7 +189,11 @@ void orc_rmi_leaf_lsq(int key_type, const uint64_t* x, uint64_t S, uint64_t V, f
   std::vector<int> freev(L + 1, 0);
   for (uint32_t j = 0; j <= L; ++j) {
     Y_out[j] = j == 0 ? 0.0 : (j > J ? (double)V : Y_init[j]);
-    freev[j] = j >= 1 && j <= J && dg[j] > 0.0;
+    freev[j] = j >= 1 && j <= J && dg[j] + rho > 0.0;
+    if (freev[j]) {
+      dg[j] += rho;
+      rhs[j] += rho * Y_init[j];
+    }
   }
   std::vector<double> bb(L + 1, 0.0);
   for (uint32_t j = 1; j <= J; ++j) {
@@ -200,15 +223,65 @@ void orc_rmi_leaf_lsq(int key_type, const uint64_t* x, uint64_t S, uint64_t V, f
   }
 }
 
-// Initial knot values: the sample's empirical CDF at each knot,
-// Y_j = V * #{sample < kb_j} / S for 1 <= j <= J; Y_0 = 0; Y_j = V for j > J.
-void orc_rmi_leaf_init(const uint64_t* x, uint64_t S, uint64_t V, uint32_t L, const uint64_t* kb, uint32_t J,
-                       double* Y) {
+void orc_rmi_leaf_project(uint64_t V, uint32_t L, uint32_t J, const double* Y0, double gamma, double* Y);
+
+// The training iteration itself: `iters` rounds of a Jacobi-preconditioned
+// gradient step Y_j <- Y_j - eta * g_j / h_j on the free knots 1..J, all
+// knots updated from the same gradient (the loss and its partials as
+// above), followed by the projection (gamma = 0 skips it), starting from
+// and regularised toward the prior Y0.  Double precision.
+void orc_rmi_leaf_train(int key_type, const uint64_t* x, uint64_t S, uint64_t V, float a, float b, uint32_t L,
+                        const uint64_t* kb, uint32_t J, const double* Y0, double rho, double gamma, uint32_t iters,
+                        double eta, double* Y_out) {
+  std::vector<double> g(L + 1), h(L + 1);
+  for (uint32_t j = 0; j <= L; ++j) Y_out[j] = Y0[j];
+  for (uint32_t it = 0; it < iters; ++it) {
+    orc_rmi_leaf_loss_grad(key_type, x, S, V, a, b, L, kb, J, Y_out, Y0, rho, g.data(), h.data());
+    for (uint32_t j = 1; j <= J; ++j)
+      if (h[j] > 0.0) Y_out[j] -= eta * g[j] / h[j];
+    if (gamma > 0.0) orc_rmi_leaf_project(V, L, J, Y0, gamma, Y_out);
+  }
+}
+
+// Prior knot values: the interpolant of the rank targets at each knot kb_j
+// (1 <= j <= J).  With lo = #{sample < kb_j}, kb_j lies in (x_{lo-1}, x_lo]
+// and Y0_j interpolates linearly in the key between the targets of those
+// two samples; the end points (0, 0) and (key max + 1, V) close the ends.
+// Y0_0 = 0, Y0_j = V for j > J.  Double, unfused, in the order written.
+void orc_rmi_leaf_init(int key_type, const uint64_t* x, uint64_t S, uint64_t V, uint32_t L, const uint64_t* kb,
+                       uint32_t J, double* Y) {
+  const uint64_t kmax = key_max(key_type);
   for (uint32_t j = 0; j <= L; ++j) {
     if (j == 0) { Y[j] = 0.0; continue; }
     if (j > J) { Y[j] = (double)V; continue; }
-    const uint64_t c = (uint64_t)(std::lower_bound(x, x + S, kb[j]) - x);
-    Y[j] = (double)V * (double)c / (double)S;
+    const uint64_t k = kb[j];
+    const uint64_t lo = (uint64_t)(std::lower_bound(x, x + S, k) - x);
+    const uint64_t xl = lo == 0 ? 0 : x[lo - 1];
+    const double yl = lo == 0 ? 0.0 : (double)(2 * lo - 1) / (double)(2 * S);
+    const double yr = lo == S ? 1.0 : (double)(2 * lo + 1) / (double)(2 * S);
+    const double num = (double)(k - xl);
+    const double den = lo == S ? (double)(kmax - xl) + 1.0 : (double)(x[lo] - xl);
+    const double f = den > 0.0 ? num / den : 0.0;
+    const double dy = yr - yl;
+    const double t = f * dy;
+    const double y = yl + t;
+    Y[j] = (double)V * y;
+  }
+}
+
+// Projection onto { Y_j - Y_{j-1} >= gamma (Y0_j - Y0_{j-1}), Y_0 = 0,
+// Y_{J+1} = V }: with Z = Y - gamma Y0 the constraint is Z non-decreasing
+// between Z_0 = 0 and (1 - gamma) V, so Z becomes its running maximum capped
+// at (1 - gamma) V.
+void orc_rmi_leaf_project(uint64_t V, uint32_t L, uint32_t J, const double* Y0, double gamma, double* Y) {
+  const double cap = (1.0 - gamma) * (double)V;
+  double run = 0.0;
+  for (uint32_t j = 1; j <= J && j <= L; ++j) {
+    const double gy = gamma * Y0[j];
+    const double z = Y[j] - gy;
+    run = std::max(run, z);
+    const double zc = std::min(run, cap);
+    Y[j] = zc + gy;
   }
 }
 

@@ -41,11 +41,15 @@ def lib():
         L.orc_rmi_knots.restype = u32
         L.orc_rmi_knots.argtypes = [f32, f32, u32, i32, vp]
         L.orc_rmi_leaf_loss_grad.restype = f64
-        L.orc_rmi_leaf_loss_grad.argtypes = [i32, vp, u64, u64, f32, f32, u32, vp, u32, vp, vp, vp]
+        L.orc_rmi_leaf_loss_grad.argtypes = [i32, vp, u64, u64, f32, f32, u32, vp, u32, vp, vp, f64, vp, vp]
         L.orc_rmi_leaf_lsq.restype = None
-        L.orc_rmi_leaf_lsq.argtypes = [i32, vp, u64, u64, f32, f32, u32, vp, u32, vp, vp]
+        L.orc_rmi_leaf_lsq.argtypes = [i32, vp, u64, u64, f32, f32, u32, vp, u32, vp, f64, vp]
+        L.orc_rmi_leaf_train.restype = None
+        L.orc_rmi_leaf_train.argtypes = [i32, vp, u64, u64, f32, f32, u32, vp, u32, vp, f64, f64, u32, f64, vp]
         L.orc_rmi_leaf_init.restype = None
-        L.orc_rmi_leaf_init.argtypes = [vp, u64, u64, u32, vp, u32, vp]
+        L.orc_rmi_leaf_init.argtypes = [i32, vp, u64, u64, u32, vp, u32, vp]
+        L.orc_rmi_leaf_project.restype = None
+        L.orc_rmi_leaf_project.argtypes = [u64, u32, u32, vp, f64, vp]
         L.orc_rmi_root_lsq.restype = None
         L.orc_rmi_root_lsq.argtypes = [i32, vp, u64, u32, vp]
         L.orc_rmi_root_loss_grad.restype = f64
@@ -82,27 +86,59 @@ def knots(a: float, b: float, L: int, key_type: int):
     return kb, int(J)
 
 
-def leaf_init(x: np.ndarray, V: int, L: int, kb: np.ndarray, J: int) -> np.ndarray:
+RIDGE = 1.0        # rho: knot-value ridge, in units of one sample's squared error
+MIN_WIDTH = 0.5    # gamma: a leaf keeps at least this share of its prior width
+ETA = 0.9          # Jacobi step size
+ITERS = 40         # default number of training rounds
+
+
+def leaf_init(x: np.ndarray, V: int, L: int, kb: np.ndarray, J: int, key_type: int = 1) -> np.ndarray:
+    """Prior knot values: the sample's rank-target interpolant at the knots."""
+    x = np.ascontiguousarray(x, dtype=np.uint64)
+    kb = np.ascontiguousarray(kb, dtype=np.uint64)
     Y = np.empty(L + 1, dtype=np.float64)
-    lib().orc_rmi_leaf_init(_ptr(x), len(x), V, L, _ptr(kb), J, _ptr(Y))
+    lib().orc_rmi_leaf_init(key_type, _ptr(x), len(x), V, L, _ptr(kb), J, _ptr(Y))
     return Y
 
 
+def leaf_project(V: int, L: int, J: int, Y0: np.ndarray, Y: np.ndarray, gamma: float = MIN_WIDTH) -> np.ndarray:
+    Y0 = np.ascontiguousarray(Y0, dtype=np.float64)
+    out = np.array(Y, dtype=np.float64, copy=True)
+    lib().orc_rmi_leaf_project(V, L, J, _ptr(Y0), gamma, _ptr(out))
+    return out
+
+
 def leaf_loss_grad(key_type: int, x: np.ndarray, V: int, a: float, b: float, L: int, kb: np.ndarray, J: int,
-                   Y: np.ndarray):
-    """(loss, grad[L+1], hessian diagonal[L+1]) in double."""
+                   Y: np.ndarray, Y0: np.ndarray | None = None, rho: float = RIDGE):
+    """(loss, grad[L+1], hessian diagonal[L+1]) in double; Y0 defaults to the
+    initial knot values of the sample."""
     Y = np.ascontiguousarray(Y, dtype=np.float64)
+    if Y0 is None:
+        Y0 = leaf_init(x, V, L, kb, J, key_type)
+    Y0 = np.ascontiguousarray(Y0, dtype=np.float64)
     g = np.empty(L + 1)
     d = np.empty(L + 1)
-    loss = lib().orc_rmi_leaf_loss_grad(key_type, _ptr(x), len(x), V, a, b, L, _ptr(kb), J, _ptr(Y), _ptr(g), _ptr(d))
+    loss = lib().orc_rmi_leaf_loss_grad(key_type, _ptr(x), len(x), V, a, b, L, _ptr(kb), J, _ptr(Y), _ptr(Y0), rho,
+                                        _ptr(g), _ptr(d))
     return float(loss), g, d
 
 
 def leaf_lsq(key_type: int, x: np.ndarray, V: int, a: float, b: float, L: int, kb: np.ndarray, J: int,
-             Y_init: np.ndarray) -> np.ndarray:
+             Y_init: np.ndarray, rho: float = RIDGE) -> np.ndarray:
     Y_init = np.ascontiguousarray(Y_init, dtype=np.float64)
     out = np.empty(L + 1)
-    lib().orc_rmi_leaf_lsq(key_type, _ptr(x), len(x), V, a, b, L, _ptr(kb), J, _ptr(Y_init), _ptr(out))
+    lib().orc_rmi_leaf_lsq(key_type, _ptr(x), len(x), V, a, b, L, _ptr(kb), J, _ptr(Y_init), rho, _ptr(out))
+    return out
+
+
+def leaf_train(key_type: int, x: np.ndarray, V: int, a: float, b: float, L: int, kb: np.ndarray, J: int,
+               Y0: np.ndarray, iters: int = ITERS, eta: float = ETA, rho: float = RIDGE,
+               gamma: float = MIN_WIDTH) -> np.ndarray:
+    """Knot values after `iters` rounds of (Jacobi step, projection) from Y0."""
+    Y0 = np.ascontiguousarray(Y0, dtype=np.float64)
+    out = np.empty(L + 1)
+    lib().orc_rmi_leaf_train(key_type, _ptr(x), len(x), V, a, b, L, _ptr(kb), J, _ptr(Y0), rho, gamma, iters, eta,
+                             _ptr(out))
     return out
 
 

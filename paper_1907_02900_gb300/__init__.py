@@ -60,6 +60,14 @@ SIGNATURES = {
     "hg_probe": (_I32, [_CFGP, _TABP, _VP, _U64, _VP, _VP]),
     "hg_probe_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
     "hg_probe_binned": (_I32, [_CFGP, _TABP, _VP, _U64, _VP, _VP, _SZ, _VP]),
+    "hg_learned_model_bytes": (_SZ, [_U32]),
+    "hg_learned_workspace_size": (_SZ, [_I32, _U64, _U64, _U32]),
+    "hg_learned_train": (_I32, [_I32, _VP, _U64, _U64, _U32, _U64, _U64, _U32, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_learned_sorted_sample": (_I32, [_I32, _VP, _U64, _U64, _U64, _VP, _VP, _SZ, _VP]),
+    "hg_learned_root_grad": (_I32, [_I32, _VP, _U64, _U32, ctypes.c_double, ctypes.c_double, _VP, _VP, _SZ, _VP]),
+    "hg_learned_leaf_grad": (_I32, [_I32, _VP, _U64, _U64, ctypes.c_float, ctypes.c_float, _U32, _VP, _VP, _VP,
+                                    _VP, _VP, _SZ, _VP]),
+    "hg_bucket_stats": (_I32, [_CFGP, _VP, _U64, _VP, _VP, _VP, _SZ, _VP]),
     "hg_static_scratch_bytes": (_SZ, []),
     "hg_build_static_scratch": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
@@ -321,3 +329,103 @@ def join_materialize(A: Table, B: Table, capacity: int | None = None, stream=Non
 
 def workspace_status(ws, stream=None) -> int:
     return int(load().hg_workspace_status(_ptr(ws), _stream_handle(stream)))
+
+
+# --------------------------------------------------------------------------
+# learned bucket map
+# --------------------------------------------------------------------------
+def learned_train(keys, num_buckets: int, num_leaves: int = 1024, sample_size: int | None = None,
+                  seed: int = 0x4C524E, iters: int = 40, stream=None):
+    """Train the learned bucket map on the GPU (hg_learned_train).  Returns
+    (model uint8 tensor, diag dict with the loss before/after, the root loss
+    and the knot values)."""
+    torch = _torch()
+    _require_cuda(keys, "keys")
+    kt = _key_type_of(keys)
+    n = keys.numel()
+    S = sample_size or max(1, n // 100)
+    lib = load()
+    model = torch.empty(int(lib.hg_learned_model_bytes(num_leaves)), dtype=torch.uint8, device=keys.device)
+    wsz = int(lib.hg_learned_workspace_size(kt, n, S, num_leaves))
+    ws = torch.empty(wsz, dtype=torch.uint8, device=keys.device)
+    diag = torch.zeros(num_leaves + 5, dtype=torch.float64, device=keys.device)
+    rc = lib.hg_learned_train(kt, _ptr(keys), n, num_buckets, num_leaves, S, seed, iters, _ptr(model), _ptr(diag),
+                              _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_learned_train")
+    d = diag.cpu().numpy()
+    return model, {"loss_before": float(d[0]), "loss_after": float(d[1]), "root_loss": float(d[2]),
+                   "Y": d[4:4 + num_leaves + 1].copy(), "sample_size": S}
+
+
+def learned_sorted_sample(keys, sample_size: int, seed: int, stream=None):
+    torch = _torch()
+    kt = _key_type_of(keys)
+    lib = load()
+    out = torch.empty(sample_size + 2, dtype=torch.uint64, device=keys.device)[:sample_size]
+    ws = torch.empty(int(lib.hg_learned_workspace_size(kt, keys.numel(), sample_size, 1)), dtype=torch.uint8,
+                     device=keys.device)
+    rc = lib.hg_learned_sorted_sample(kt, _ptr(keys), keys.numel(), sample_size, seed, _ptr(out), _ptr(ws),
+                                      ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_learned_sorted_sample")
+    return out
+
+
+def learned_root_grad(key_type: int, sorted_sample, num_leaves: int, a: float, b: float, stream=None):
+    torch = _torch()
+    out = torch.empty(4, dtype=torch.float64, device=sorted_sample.device)
+    ws = torch.empty(1 << 16, dtype=torch.uint8, device=sorted_sample.device)
+    rc = load().hg_learned_root_grad(key_type, _ptr(sorted_sample), sorted_sample.numel(), num_leaves, a, b,
+                                     _ptr(out), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_learned_root_grad")
+    o = out.cpu().numpy()
+    return float(o[0]), float(o[1]), float(o[2])
+
+
+def learned_leaf_grad(key_type: int, sorted_sample, num_buckets: int, a: float, b: float, num_leaves: int, Y,
+                      stream=None):
+    """(loss, dL/dY float32[L+1], Hessian diagonal float32[L+1]) at knot values Y (float64[L+1])."""
+    torch = _torch()
+    dev = sorted_sample.device
+    lib = load()
+    S = sorted_sample.numel()
+    Yd = torch.as_tensor(Y, dtype=torch.float64).to(dev)
+    g = torch.empty(num_leaves + 1, dtype=torch.float32, device=dev)
+    h = torch.empty(num_leaves + 1, dtype=torch.float32, device=dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    ws = torch.empty(int(lib.hg_learned_workspace_size(key_type, S, S, num_leaves)), dtype=torch.uint8, device=dev)
+    rc = lib.hg_learned_leaf_grad(key_type, _ptr(sorted_sample), S, num_buckets, a, b, num_leaves, _ptr(Yd), _ptr(g),
+                                  _ptr(h), _ptr(loss), _ptr(ws), ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_learned_leaf_grad")
+    return float(loss.item()), g.cpu().numpy(), h.cpu().numpy()
+
+
+def bucket_stats(keys, num_buckets: int, model=None, seed: int = 0, stream=None) -> dict:
+    """Bucket-length max / mean / variance / non-empty count of a map over keys."""
+    torch = _torch()
+    kt = _key_type_of(keys)
+    cfg = make_config(kt, num_buckets, seed, "auto", model)
+    counts = torch.empty(num_buckets, dtype=torch.uint32, device=keys.device)
+    out = torch.empty(4, dtype=torch.float64, device=keys.device)
+    ws = torch.empty(1 << 16, dtype=torch.uint8, device=keys.device)
+    rc = load().hg_bucket_stats(ctypes.byref(cfg), _ptr(keys), keys.numel(), _ptr(counts), _ptr(out), _ptr(ws),
+                                ws.numel(), _stream_handle(stream))
+    _check(rc, "hg_bucket_stats")
+    o = out.cpu().numpy()
+    return {"max": float(o[0]), "mean": float(o[1]), "var": float(o[2]), "nonempty": float(o[3])}
+
+
+# Fallback rule of the learned map: Murmur judges it.  The learned map is
+# kept only while its bucket lengths stay close to Murmur's on the same keys.
+LEARNED_VAR_TOLERANCE = 1.25   # variance at most this multiple of Murmur's
+LEARNED_MAX_FACTOR = 4.0       # longest bucket at most this multiple of Murmur's
+
+
+def choose_map(keys, num_buckets: int, model, seed: int = 0, var_tolerance: float = LEARNED_VAR_TOLERANCE,
+               max_factor: float = LEARNED_MAX_FACTOR, stream=None):
+    """(model or None, report): the learned model if its bucket-length variance
+    and maximum over `keys` stay within the tolerances of Murmur's, else None
+    (use Murmur).  Both maps are evaluated on the GPU (hg_bucket_stats)."""
+    sl = bucket_stats(keys, num_buckets, model=model, stream=stream)
+    sm = bucket_stats(keys, num_buckets, seed=seed, stream=stream)
+    keep = sl["var"] <= var_tolerance * sm["var"] and sl["max"] <= max_factor * sm["max"]
+    return (model if keep else None), {"learned": sl, "murmur": sm, "kept": bool(keep)}

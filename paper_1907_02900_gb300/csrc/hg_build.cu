@@ -1194,6 +1194,105 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   return last_launch_status();
 }
 
+// ===========================================================================
+// LSD radix sort of uint64 keys (used for the learned map's key sample):
+// eight stable passes of the same histogram -> scan -> stable tile partition
+// pipeline, with the "bucket" of a key being one of its bytes.
+// ===========================================================================
+struct RadixByteMap {
+  uint32_t shift;
+  __device__ __forceinline__ void init() {}
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K key) const {
+    return (uint32_t)(((uint64_t)key >> shift) & 255u);
+  }
+};
+
+static void radix_layout(uint64_t n, uint64_t* chunk, uint32_t* G, size_t* o) {
+  const int sms = std::max(dev_info().sms, 1);
+  uint64_t c = std::max<uint64_t>(kPartTile, (n + 2 * sms - 1) / (2 * sms));
+  c = (c + 15) / 16 * 16;
+  *chunk = c;
+  *G = (uint32_t)std::max<uint64_t>(1, (n + c - 1) / c);
+  size_t off = sizeof(WsHeader);
+  o[0] = off; off = align_up(off + (size_t)*G * 256 * 4);  // H
+  o[1] = off; off = align_up(off + (size_t)*G * 256 * 4);  // C
+  o[2] = off; off = align_up(off + 256 * 4);               // column totals
+  o[3] = off; off = align_up(off + 257 * 4);               // digit starts
+  o[4] = off; off = align_up(off + 256 * 4 + 16);          // unused list + scratch word
+  o[5] = off; off = align_up(off + (n + 16) * 8);          // ping-pong keys
+  o[6] = off; off = align_up(off + (n + 16) * 4);          // payload (positions, unused)
+  o[7] = off;
+}
+
+size_t radix_sort_workspace_bytes(uint64_t n) {
+  uint64_t chunk;
+  uint32_t G;
+  size_t o[8];
+  radix_layout(n, &chunk, &G, o);
+  return o[7];
+}
+
+hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t st) {
+  if (n <= 1) return HG_OK;
+  uint64_t chunk;
+  uint32_t G;
+  size_t o[8];
+  radix_layout(n, &chunk, &G, o);
+  WsHeader* hdr = (WsHeader*)ws;
+  uint32_t* H = (uint32_t*)(ws + o[0]);
+  uint32_t* C = (uint32_t*)(ws + o[1]);
+  uint32_t* CT = (uint32_t*)(ws + o[2]);
+  uint32_t* BS = (uint32_t*)(ws + o[3]);
+  uint32_t* ovf = (uint32_t*)(ws + o[4]);
+  uint64_t* tmp = (uint64_t*)(ws + o[5]);
+  uint32_t* ids = (uint32_t*)(ws + o[6]);
+  uint64_t* src = keys;
+  uint64_t* dst = tmp;
+  const size_t psm = part_smem_bytes(8, false, kPartIPT, false);
+  auto kp = k_partition<uint64_t, RadixByteMap, false, kPartIPT>;
+  set_smem_once(kp, psm);
+  auto kh = k_hist<uint64_t, RadixByteMap>;
+  set_smem_once(kh, 1024);
+  for (uint32_t pass = 0; pass < 8; ++pass) {
+    RadixByteMap map{8 * pass};
+    {
+      HG_TRACE("k_radix_hist", st);
+      kh<<<G, kHistThreads, 1024, st>>>(src, n, chunk, 0, 256, 0, 256, H, C, map);
+    }
+    {
+      HG_TRACE("k_radix_scan", st);
+      k_colscan<<<1, 256, 0, st>>>(C, G, 256, CT);
+      k_scan_bins<<<1, 1024, 0, st>>>(CT, 256, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + 256, 0, (uint32_t)n);
+    }
+    PartArgs<uint64_t> pa{};
+    pa.in_k = src;
+    pa.in_i = nullptr;
+    pa.out_k = dst;
+    pa.out_i = ids;
+    pa.n = n;
+    pa.chunk = chunk;
+    pa.G = G;
+    pa.s = 0;
+    pa.sshift = 0;
+    pa.nbins = 256;
+    pa.nsb = 256;
+    pa.H = H;
+    pa.C = C;
+    pa.CT = CT;
+    pa.BS = BS;
+    pa.status = &hdr->status;
+    {
+      HG_TRACE("k_radix_partition", st);
+      kp<<<G, kPartNW * 32, psm, st>>>(pa, map);
+    }
+    uint64_t* t = src;
+    src = dst;
+    dst = t;
+  }
+  return last_launch_status();  // eight passes: the result is back in keys
+}
+
 // Explicit instantiations used by hg_api.cu (build entry point).
 #define HG_INST(K, M)                                                                                   \
   template hg_status build_v2<K, M>(const Plan&, const K*, const uint32_t*, uint32_t*, K*, uint32_t*, \

@@ -65,6 +65,8 @@ struct ProbePlan {
   size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, total;
 };
 bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePlan* p);
+size_t radix_sort_workspace_bytes(uint64_t n);
+hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t st);
 template <typename K, typename Map>
 hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, const K* queries, uint64_t q,
                             uint32_t* counts, uint8_t* ws, cudaStream_t st, Map map);

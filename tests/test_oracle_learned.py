@@ -84,8 +84,9 @@ def test_leaf_gradient_matches_finite_differences(lrn):
     assert loss >= 0
 
 
-def test_leaf_lsq_matches_explicit_least_squares(lrn):
-    keys, x, a, b, kb, J, L, V = _setup(lrn, n=5_000, S=600, L=16, V=4096)
+@pytest.mark.parametrize("n,S,L", [(5_000, 600, 16), (40_000, 400, 256)])
+def test_leaf_lsq_matches_explicit_least_squares(lrn, n, S, L):
+    keys, x, a, b, kb, J, L, V = _setup(lrn, n=n, S=S, L=L, V=4096)
     Y0 = lrn.leaf_init(x, V, L, kb, J)
     Y = lrn.leaf_lsq(1, x, V, a, b, L, kb, J, Y0)
     # explicit design matrix over the free knots 1..J
@@ -101,13 +102,96 @@ def test_leaf_lsq_matches_explicit_least_squares(lrn):
         rows[i, j + 1] += lam
     fixed = np.zeros(L + 1)
     fixed[J + 1:] = V
-    free = [j for j in range(1, J + 1) if rows[:, j].any()]
+    free = list(range(1, J + 1))
     rhs = t - rows @ fixed
-    sol, *_ = np.linalg.lstsq(rows[:, free], rhs, rcond=None)
+    # ridge rows sqrt(rho) * (Y_j - Y0_j) for the free knots
+    rho = lrn.RIDGE
+    R = np.sqrt(rho) * np.eye(len(free))
+    sol, *_ = np.linalg.lstsq(np.vstack([rows[:, free], R]), np.concatenate([rhs, np.sqrt(rho) * Y0[free]]), rcond=None)
     assert np.allclose(Y[free], sol, rtol=1e-7, atol=1e-6)
     # stationarity: zero gradient on the free knots at the optimum
     _, g, _ = lrn.leaf_loss_grad(1, x, V, a, b, L, kb, J, Y)
     assert np.max(np.abs(g[free])) < 1e-6 * V
+
+
+def test_leaf_train_steps_and_converges(lrn):
+    # sparse: about two samples per leaf, so some knot runs converge slowly
+    keys, x, a, b, kb, J, L, V = _setup(lrn, n=40_000, S=500, L=256, V=1 << 14)
+    Y0 = lrn.leaf_init(x, V, L, kb, J)
+    # one round without projection is the preconditioned gradient step on the free knots only
+    _, g, d = lrn.leaf_loss_grad(1, x, V, a, b, L, kb, J, Y0)
+    step = Y0.copy()
+    step[1:J + 1] -= 0.9 * g[1:J + 1] / d[1:J + 1]
+    assert np.allclose(lrn.leaf_train(1, x, V, a, b, L, kb, J, Y0, 1, gamma=0.0), step, rtol=0, atol=1e-9 * V)
+    # with projection: the same step, then the projection
+    want = lrn.leaf_project(V, L, J, Y0, step)
+    assert np.allclose(lrn.leaf_train(1, x, V, a, b, L, kb, J, Y0, 1), want, rtol=0, atol=1e-9 * V)
+    # unprojected, the iteration is a contraction toward the closed-form optimum
+    Yl = lrn.leaf_lsq(1, x, V, a, b, L, kb, J, Y0)
+    e = [np.abs(lrn.leaf_train(1, x, V, a, b, L, kb, J, Y0, it, gamma=0.0) - Yl).max() for it in (3, 30, 3000)]
+    assert e[0] > e[1] > e[2] and e[2] < 1e-6 * V
+    # projected, it lowers the loss from the prior but cannot beat the unconstrained optimum
+    Yt = lrn.leaf_train(1, x, V, a, b, L, kb, J, Y0, 40)
+    l0, l1, ll = (lrn.leaf_loss_grad(1, x, V, a, b, L, kb, J, Y)[0] for Y in (Y0, Yt, Yl))
+    assert ll <= l1 < l0
+    Yfull = np.append(Yt[:J + 1], V)
+    P0 = np.append(Y0[:J + 1], V)
+    assert np.all(np.diff(Yfull) >= 0.5 * np.diff(P0) - 1e-9 * V)
+
+
+def test_leaf_init_interpolates_the_rank_targets(lrn):
+    rng = np.random.default_rng(3)
+    x = np.sort(rng.choice(1 << 40, size=200, replace=False).astype(np.uint64))
+    S, V = len(x), 1 << 16
+    t = V * (2 * np.arange(S) + 1) / (2 * S)
+    # knots at sample points hit their targets; midpoints of neighbours give the mean
+    kb = np.concatenate([[0], x[::7], (x[10:60:5] // 2 + x[11:61:5] // 2)]).astype(np.uint64)
+    kb = np.sort(kb)
+    J = len(kb) - 1
+    Y = lrn.leaf_init(x, V, J, kb, J)
+    assert Y[0] == 0
+    for j in range(1, J + 1):
+        k = int(kb[j])
+        i = int(np.searchsorted(x, kb[j]))
+        if i < S and int(x[i]) == k:
+            assert abs(Y[j] - t[i]) <= 1e-9 * V
+        else:
+            lam = (k - int(x[i - 1])) / (int(x[i]) - int(x[i - 1]))
+            assert abs(Y[j] - ((1 - lam) * t[i - 1] + lam * t[i])) <= 1e-9 * V
+    assert np.all(np.diff(Y) > 0)
+    # the ends: below the first sample toward (0, 0), above the last toward (key max + 1, V)
+    kb2 = np.array([0, int(x[0]) // 2, int(x[-1]) + ((1 << 64) - 1 - int(x[-1])) // 2], dtype=np.uint64)
+    Y2 = lrn.leaf_init(x, V, 2, kb2, 2)
+    assert abs(Y2[1] - t[0] * (int(x[0]) // 2) / int(x[0])) <= 1e-9 * V
+    assert abs(Y2[2] - (t[-1] + (V - t[-1]) * 0.5)) <= 1e-6 * V
+    # knots above J sit at V
+    Y3 = lrn.leaf_init(x, V, 5, kb[:6], 3)
+    assert np.all(Y3[4:] == V)
+
+
+def test_leaf_project_is_the_least_feasible_majorant(lrn):
+    rng = np.random.default_rng(4)
+    V, L, gam = 1000, 12, 0.5
+    for trial in range(50):
+        J = int(rng.integers(1, L + 1))
+        Y0 = np.concatenate([[0.0], np.sort(rng.uniform(0, V, L))])
+        Y0[J + 1:] = V
+        Y = Y0 + rng.normal(0, 60, L + 1)
+        Y[0] = 0
+        P = lrn.leaf_project(V, L, J, Y0, Y, gam)
+        Z, Zp = Y - gam * Y0, P - gam * Y0
+        Zp0, Zj = Zp[:J + 1], Z[:J + 1]
+        # feasible: Z' non-decreasing from 0 and capped so that the last leaf keeps its floor
+        assert np.all(np.diff(np.concatenate([[0.0], Zp0[1:]])) >= -1e-12)
+        assert np.all(Zp0[1:] <= (1 - gam) * V + 1e-9)
+        # every value is attained: either the cap or an earlier Z (or 0)
+        for j in range(1, J + 1):
+            cands = np.concatenate([[0.0], Zj[1:j + 1], [(1 - gam) * V]])
+            assert np.min(np.abs(cands - Zp0[j])) <= 1e-9
+            assert Zp0[j] >= min(Zj[j], (1 - gam) * V) - 1e-12
+        # knots above J untouched; feasible inputs unchanged (idempotent)
+        assert np.array_equal(P[J + 1:], Y[J + 1:])
+        assert np.allclose(lrn.leaf_project(V, L, J, Y0, P, gam), P, rtol=0, atol=1e-9)
 
 
 def test_root_fit_and_gradient(lrn):
