@@ -193,6 +193,67 @@ hg_status hg_learned_leaf_grad(int32_t key_type, const uint64_t* d_sorted, uint6
 hg_status hg_bucket_stats(const hg_config* cfg, const void* d_keys, uint64_t n, uint32_t* d_counts,
                           double* d_out4, void* d_ws, size_t ws_bytes, void* stream);
 
+/* -------------------------------------------------------------- batched --
+ * Many independent tables of uneven sizes built and probed together.  The
+ * paper builds one table per call; batching is not in it.  Table t has n_t
+ * uint32 keys (ids 0..n_t-1, their positions), V_t >= 1 buckets (Eq. 1 with
+ * its own V_t and the common seed) and q_t queries.  Device arrays are the
+ * concatenation over t = 0..T-1 at the positions hg_batch_layout returns
+ * (each table's keys and queries start on a 16-byte boundary; up to 3
+ * padding slots follow a table and are ignored):
+ *   keys      [totals[0]] uint32, table t at key_begin[t]
+ *   queries   [totals[1]] uint32, table t at query_begin[t]
+ *   offsets   [totals[2]] uint32; table t's V_t + 1 offsets start at
+ *             offset_begin[t] and are positions in the concatenated CSR
+ *             arrays: bucket v of table t is [offsets[ob+v], offsets[ob+v+1])
+ *   csr_keys, csr_ids  [totals[0]]; ids are table-local
+ *   counts    [totals[1]] uint32: matches of each query in its own table
+ * Table t equals the table hg_build makes from its keys alone, every offset
+ * raised by key_begin[t]; counts equal hg_probe's.  The caller owns every
+ * buffer; the plan (host memory) owns a CUDA stream, two events and the
+ * cached graph.  Arguments are checked synchronously; device errors
+ * (timeouts) are read with hg_workspace_status(d_ws).
+ * hg_batch_plan_create: host only.  h_num_buckets NULL means V_t =
+ *   max(1, n_t).  Totals below 2^32.  Key type uint32 only (uint64:
+ *   HG_ERR_UNSUPPORTED).
+ * hg_batch_run: enqueues the batch on `stream`.  Tables are grouped into
+ *   waves whose buckets fit 2^15 bins of the bin size; per wave one
+ *   two-level build (Alg. 2) and one binned probe over the wave's slice of
+ *   the common bucket space.  The launch sequence is captured into a CUDA
+ *   graph on the first call with a given set of buffers and configuration
+ *   and replayed by later calls with the same ones.
+ * hg_batch_autotune: synchronous; times `reps` runs of every candidate (bin
+ *   shift near the automatic one x 512 / 1024 threads per bin) on the given
+ *   buffers, keeps the fastest and returns its time.  Results do not depend
+ *   on the configuration.
+ * hg_batch_run_plain: the same work as a host loop of hg_build + hg_probe,
+ *   one table at a time (offsets then table-local), for comparison.
+ * Workspace: hg_batch_workspace_size(plan) bytes, 256-byte aligned, for all
+ * three calls. */
+typedef struct hg_batch_plan hg_batch_plan;
+hg_status hg_batch_plan_create(int32_t key_type, uint32_t seed, uint32_t num_tables,
+                               const uint64_t* h_table_sizes, const uint64_t* h_query_sizes,
+                               const uint64_t* h_num_buckets, hg_batch_plan** out);
+void hg_batch_plan_destroy(hg_batch_plan* plan);
+/* h_totals4: keys, queries, offset entries, tables; each *_begin (T+1
+ * entries) may be NULL */
+hg_status hg_batch_layout(const hg_batch_plan* plan, uint64_t* h_totals4, uint64_t* h_key_begin,
+                          uint64_t* h_query_begin, uint64_t* h_offset_begin);
+size_t hg_batch_workspace_size(const hg_batch_plan* plan);
+/* bin_shift 0 / threads_per_bin 0 = automatic */
+hg_status hg_batch_set_config(hg_batch_plan* plan, uint32_t bin_shift, uint32_t threads_per_bin);
+hg_status hg_batch_get_config(const hg_batch_plan* plan, uint32_t* bin_shift, uint32_t* threads_per_bin,
+                              uint32_t* waves);
+hg_status hg_batch_run(hg_batch_plan* plan, const void* d_keys, const void* d_queries, uint32_t* d_offsets,
+                       void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts, void* d_ws,
+                       size_t ws_bytes, void* stream);
+hg_status hg_batch_autotune(hg_batch_plan* plan, const void* d_keys, const void* d_queries,
+                            uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts,
+                            void* d_ws, size_t ws_bytes, void* stream, uint32_t reps, float* h_best_ms);
+hg_status hg_batch_run_plain(hg_batch_plan* plan, const void* d_keys, const void* d_queries,
+                             uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts,
+                             void* d_ws, size_t ws_bytes, void* stream);
+
 /* ------------------------------------------------ build, no allocation --
  * The paper has no counterpart of this entry point.  It is hg_build (V2)
  * for callers that cannot allocate device memory -- code running inside a

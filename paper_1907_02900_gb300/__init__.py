@@ -68,6 +68,15 @@ SIGNATURES = {
     "hg_learned_leaf_grad": (_I32, [_I32, _VP, _U64, _U64, ctypes.c_float, ctypes.c_float, _U32, _VP, _VP, _VP,
                                     _VP, _VP, _SZ, _VP]),
     "hg_bucket_stats": (_I32, [_CFGP, _VP, _U64, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_batch_plan_create": (_I32, [_I32, _U32, _U32, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
+    "hg_batch_plan_destroy": (None, [_VP]),
+    "hg_batch_layout": (_I32, [_VP, _VP, _VP, _VP, _VP]),
+    "hg_batch_workspace_size": (_SZ, [_VP]),
+    "hg_batch_set_config": (_I32, [_VP, _U32, _U32]),
+    "hg_batch_get_config": (_I32, [_VP, _VP, _VP, _VP]),
+    "hg_batch_run": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_batch_autotune": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _U32, _VP]),
+    "hg_batch_run_plain": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_static_scratch_bytes": (_SZ, []),
     "hg_build_static_scratch": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
@@ -429,3 +438,107 @@ def choose_map(keys, num_buckets: int, model, seed: int = 0, var_tolerance: floa
     sm = bucket_stats(keys, num_buckets, seed=seed, stream=stream)
     keep = sl["var"] <= var_tolerance * sm["var"] and sl["max"] <= max_factor * sm["max"]
     return (model if keep else None), {"learned": sl, "murmur": sm, "kept": bool(keep)}
+
+
+class BatchPlan:
+    """Many independent uint32 tables built and probed together
+    (hg_batch_*).  Table t has sizes[t] keys, qsizes[t] queries and
+    num_buckets[t] buckets (default max(1, sizes[t])).  Buffers live in one
+    padded concatenated layout (see ``alloc``); ``run`` replays one CUDA
+    graph for the whole batch."""
+
+    def __init__(self, sizes, qsizes, num_buckets=None, seed: int = 0):
+        import numpy as np
+        lib = load()
+        self._lib = lib
+        self.T = len(sizes)
+        self.seed = seed & 0xFFFFFFFF
+        self.sizes = np.ascontiguousarray(sizes, dtype=np.uint64)
+        self.qsizes = np.ascontiguousarray(qsizes, dtype=np.uint64)
+        self.V = None if num_buckets is None else np.ascontiguousarray(num_buckets, dtype=np.uint64)
+        h = _VP()
+        rc = lib.hg_batch_plan_create(KEY_U32, seed & 0xFFFFFFFF, self.T, self.sizes.ctypes.data,
+                                      self.qsizes.ctypes.data, None if self.V is None else self.V.ctypes.data,
+                                      ctypes.byref(h))
+        _check(rc, "hg_batch_plan_create")
+        self._h = h
+        tot = np.zeros(4, dtype=np.uint64)
+        self.key_begin = np.zeros(self.T + 1, dtype=np.uint64)
+        self.query_begin = np.zeros(self.T + 1, dtype=np.uint64)
+        self.offset_begin = np.zeros(self.T + 1, dtype=np.uint64)
+        _check(lib.hg_batch_layout(h, tot.ctypes.data, self.key_begin.ctypes.data, self.query_begin.ctypes.data,
+                                   self.offset_begin.ctypes.data), "hg_batch_layout")
+        self.total_keys, self.total_queries, self.total_offsets = int(tot[0]), int(tot[1]), int(tot[2])
+        self.ws_bytes = int(lib.hg_batch_workspace_size(h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.hg_batch_plan_destroy(h)
+            self._h = None
+
+    def num_buckets(self, t: int) -> int:
+        return int(self.offset_begin[t + 1] - self.offset_begin[t]) - 1
+
+    def alloc(self, device="cuda") -> dict:
+        """Device buffers of the batch: keys, queries, offsets, csr_keys, csr_ids, counts, ws."""
+        torch = _torch()
+        u32 = torch.uint32
+        return {"keys": torch.zeros(self.total_keys + 4, dtype=u32, device=device)[:self.total_keys],
+                "queries": torch.zeros(self.total_queries + 4, dtype=u32, device=device)[:self.total_queries],
+                "offsets": torch.empty(self.total_offsets, dtype=u32, device=device),
+                "csr_keys": torch.empty(self.total_keys + 4, dtype=u32, device=device)[:self.total_keys],
+                "csr_ids": torch.empty(self.total_keys + 4, dtype=u32, device=device)[:self.total_keys],
+                "counts": torch.empty(self.total_queries + 4, dtype=u32, device=device)[:self.total_queries],
+                "ws": torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)}
+
+    def pad_keys(self, flat):
+        """Host array of all tables' keys back to back (unpadded) -> padded layout."""
+        import numpy as np
+        out = np.zeros(self.total_keys, dtype=np.uint32)
+        ub = np.concatenate([[0], np.cumsum(self.sizes.astype(np.int64))])
+        out[np.repeat(self.key_begin[:-1].astype(np.int64) - ub[:-1], self.sizes.astype(np.int64))
+            + np.arange(int(ub[-1]))] = flat
+        return out
+
+    def pad_queries(self, flat):
+        import numpy as np
+        out = np.zeros(self.total_queries, dtype=np.uint32)
+        ub = np.concatenate([[0], np.cumsum(self.qsizes.astype(np.int64))])
+        out[np.repeat(self.query_begin[:-1].astype(np.int64) - ub[:-1], self.qsizes.astype(np.int64))
+            + np.arange(int(ub[-1]))] = flat
+        return out
+
+    def _args(self, b):
+        for k in ("keys", "queries", "offsets", "csr_keys", "csr_ids", "counts", "ws"):
+            _require_cuda(b[k], k)
+        return (_ptr(b["keys"]), _ptr(b["queries"]), _ptr(b["offsets"]), _ptr(b["csr_keys"]), _ptr(b["csr_ids"]),
+                _ptr(b["counts"]), _ptr(b["ws"]), b["ws"].numel())
+
+    def run(self, b: dict, stream=None):
+        _check(self._lib.hg_batch_run(self._h, *self._args(b), _stream_handle(stream)), "hg_batch_run")
+
+    def run_plain(self, b: dict, stream=None):
+        _check(self._lib.hg_batch_run_plain(self._h, *self._args(b), _stream_handle(stream)), "hg_batch_run_plain")
+
+    def autotune(self, b: dict, reps: int = 2, stream=None) -> dict:
+        ms = ctypes.c_float(0.0)
+        _check(self._lib.hg_batch_autotune(self._h, *self._args(b), _stream_handle(stream), reps, ctypes.byref(ms)),
+               "hg_batch_autotune")
+        return dict(self.config(), ms=ms.value)
+
+    def set_config(self, bin_shift: int = 0, threads_per_bin: int = 0):
+        _check(self._lib.hg_batch_set_config(self._h, bin_shift, threads_per_bin), "hg_batch_set_config")
+
+    def config(self) -> dict:
+        s, t, w = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        _check(self._lib.hg_batch_get_config(self._h, ctypes.byref(s), ctypes.byref(t), ctypes.byref(w)),
+               "hg_batch_get_config")
+        return {"bin_shift": s.value, "threads_per_bin": t.value, "waves": w.value}
+
+    def table(self, b: dict, t: int):
+        """Views of table t: (offsets[V_t+1] as positions in the batch, csr keys, csr ids, counts)."""
+        k0, k1 = int(self.key_begin[t]), int(self.key_begin[t]) + int(self.sizes[t])
+        q0, q1 = int(self.query_begin[t]), int(self.query_begin[t]) + int(self.qsizes[t])
+        o0, o1 = int(self.offset_begin[t]), int(self.offset_begin[t + 1])
+        return b["offsets"][o0:o1], b["csr_keys"][k0:k1], b["csr_ids"][k0:k1], b["counts"][q0:q1]

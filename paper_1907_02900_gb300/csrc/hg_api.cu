@@ -39,7 +39,8 @@ hg_status validate_config(const hg_config* cfg) {
   if (cfg->algo < HG_ALGO_AUTO || cfg->algo > HG_ALGO_V2) return HG_ERR_INVALID_ARG;
   if (cfg->map == HG_MAP_LEARNED && !cfg->d_model) return HG_ERR_MODEL;
   if (cfg->bin_shift > kMaxBinShift) return HG_ERR_INVALID_ARG;
-  if (cfg->threads_per_bin != 0 && cfg->threads_per_bin != 1024) return HG_ERR_UNSUPPORTED;
+  if (cfg->threads_per_bin != 0 && cfg->threads_per_bin != 512 && cfg->threads_per_bin != 1024)
+    return HG_ERR_UNSUPPORTED;
   return HG_OK;
 }
 

@@ -62,6 +62,7 @@ bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
   p->n = n;
   p->V = cfg->num_buckets;
   p->emax = p->kb == 4 ? kBinEmaxU32 : kBinEmaxU64;
+  p->tpb = cfg->threads_per_bin == 512 ? 512u : 1024u;
   const uint64_t V = p->V;
   int s;
   if (cfg->bin_shift) {
@@ -141,17 +142,20 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const K* __restrict__ key
     for (int u = 0; u < 4; ++u) {
       K k[per];
       unpack16<K>(x[u], k);
+      const uint32_t p0 = (uint32_t)((v + u * bd) * per);
 #pragma unroll
-      for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e]) >> s], 1u);
+      for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e], p0 + e) >> s], 1u);
     }
   }
   for (; v < v1; v += bd) {
     K k[per];
     unpack16<K>(__ldcs(kv + v), k);
+    const uint32_t p0 = (uint32_t)(v * per);
 #pragma unroll
-    for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e]) >> s], 1u);
+    for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e], p0 + e) >> s], 1u);
   }
-  for (uint64_t i = max(v1 * per, c0) + threadIdx.x; i < c1; i += bd) atomicAdd(&hist[map(keys[i]) >> s], 1u);
+  for (uint64_t i = max(v1 * per, c0) + threadIdx.x; i < c1; i += bd)
+    atomicAdd(&hist[map(keys[i], (uint32_t)i) >> s], 1u);
   __syncthreads();
   uint32_t* row = H + (uint64_t)blockIdx.x * nbins;
   for (uint32_t i = threadIdx.x; i < nbins; i += bd) row[i] = hist[i];
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ ovf_list,
                                                     uint32_t* __restrict__ ovf_count,
                                                     uint32_t* __restrict__ offsets, uint64_t V,
-                                                    uint32_t n) {
+                                                    uint32_t n_end) {
   __shared__ uint32_t wsum[32];
   const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
   const uint32_t b = threadIdx.x * per, e = min(b + per, nbins);
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
   }
   if (threadIdx.x == 0) {
     BS[nbins] = total;
-    offsets[V] = n;
+    offsets[V] = n_end;
   }
 }
 
@@ -387,7 +391,7 @@ __global__ void __launch_bounds__(kPartNW * 32, kPartMinBlocks) k_partition(Part
       if (idx < cnt) {
         key[r] = kk[idx];
         val[r] = has_ids ? ii[idx] : (uint32_t)(cur.t0 + idx);
-        const uint32_t bucket = map(key[r]);
+        const uint32_t bucket = map(key[r], val[r]);
         dig[r] = PASS_B ? (bucket >> a.s) - (sb << a.sshift) : bucket >> (a.s + a.sshift);
       } else {
         key[r] = 0;
@@ -415,6 +419,7 @@ struct BinArgs {
   const uint32_t* BS;
   uint64_t V;
   uint32_t nbins, s, emax;
+  uint32_t pos_base;  // added to every offset written (position of element 0 in the CSR arrays)
   int nbuf;  // staging buffers: 2 = next bin prefetched during this one
   uint32_t* status;
 };
@@ -429,8 +434,8 @@ struct BinArgs {
 //      order because both partition passes are stable: insertion sort for
 //      up to kBinSmallBucket edges, a per-warp position bitmap above
 //   5. the edges are written out in slot order (coalesced)
-template <typename K, typename Map>
-__global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map map) {
+template <typename K, typename Map, int NWB>
+__global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map) {
   const uint32_t EB = a.emax + 16;
   const int nbuf = a.nbuf;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -511,7 +516,7 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map m
     const uint32_t* ii = iin[buf] + (start - si_.a0);
     // 1. local buckets and counts
     for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
-      const uint32_t l = map(kk[e]) - (uint32_t)bucket0;
+      const uint32_t l = map(kk[e], ii[e]) - (uint32_t)bucket0;
       lb[e] = (uint16_t)l;
       atomicAdd(&cnt[l >> 1], 1u << ((l & 1u) << 4));
     }
@@ -529,8 +534,8 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map m
       for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
         const uint32_t v = 2 * w;
-        a.offsets[bucket0 + v] = start + base;
-        if (v + 1 < nb) a.offsets[bucket0 + v + 1] = start + base + lo;
+        a.offsets[bucket0 + v] = a.pos_base + start + base;
+        if (v + 1 < nb) a.offsets[bucket0 + v + 1] = a.pos_base + start + base + lo;
         cnt[w] = base | ((base + lo) << 16);
         base += lo + hi;
       }
@@ -601,7 +606,7 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild(BinArgs<K> a, Map m
     for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
       const uint32_t p = opos[j];
       a.csr_k[start + j] = kk[p];
-      a.csr_i[start + j] = ii[p];
+      a.csr_i[start + j] = map.out_id(ii[p]);
     }
     __syncthreads();
     if (nbuf == 1 && jb_next < nmine) issue(jb_next, 0);
@@ -640,11 +645,11 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
     for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) cur[v] = 0;
     __syncthreads();
     for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
-      atomicAdd(&cur[map(a.in_k[start + e]) - (uint32_t)bucket0], 1u);
+      atomicAdd(&cur[map(a.in_k[start + e], a.in_i[start + e]) - (uint32_t)bucket0], 1u);
     __syncthreads();
     block_excl_scan_smem(cur, (int)nb, wsum);
     for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
-      a.offsets[bucket0 + v] = start + cur[v];
+      a.offsets[bucket0 + v] = a.pos_base + start + cur[v];
       cur[v] += start;
     }
     __syncthreads();
@@ -652,9 +657,10 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
       const uint32_t cnt = min((uint32_t)kBigTile, E - t0);
       for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
         const K key = a.in_k[start + t0 + e];
+        const uint32_t id = a.in_i[start + t0 + e];
         tk[e] = key;
-        ti[e] = a.in_i[start + t0 + e];
-        lb[e] = (uint16_t)(map(key) - (uint32_t)bucket0);
+        ti[e] = id;
+        lb[e] = (uint16_t)(map(key, id) - (uint32_t)bucket0);
       }
       __syncthreads();
       const uint16_t* sorted = sort_positions_by_bucket<IPT, NW>(lb, cnt, nb, tmp, perm, wc, wsum);
@@ -670,7 +676,7 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
         const uint32_t g = cur[l] + (j - lo);
         const uint32_t p = sorted[j];
         a.csr_k[g] = tk[p];
-        a.csr_i[g] = ti[p];
+        a.csr_i[g] = map.out_id(ti[p]);
       }
       __syncthreads();
       for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
@@ -828,7 +834,7 @@ static void set_smem_once(F* kernel, size_t bytes) {
 
 template <typename K, typename Map>
 hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
-                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map) {
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map, uint32_t pos_base) {
   WsHeader* hdr = (WsHeader*)ws;
   uint32_t* status = &hdr->status;
   uint32_t* H = (uint32_t*)(ws + p.o_H);
@@ -861,7 +867,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   const bool two = p.sshift > 0;
   {
     HG_TRACE("k_scan_bins", st);
-    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, p.emax, ovf, &hdr->ovf_count, offsets, p.V, (uint32_t)p.n);
+    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, p.emax, ovf, &hdr->ovf_count, offsets, p.V,
+                                    pos_base + (uint32_t)p.n);
   }
 
   PartArgs<K> pa{};
@@ -928,6 +935,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   ba.nbins = p.nbins;
   ba.s = p.s;
   ba.emax = p.emax;
+  ba.pos_base = pos_base;
   ba.status = status;
   {
     size_t sm = bin_smem_bytes(sizeof(K), p.emax, p.s, 2);
@@ -936,12 +944,16 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
       sm = bin_smem_bytes(sizeof(K), p.emax, p.s, 1);
       ba.nbuf = 1;
     }
-    auto kern = k_binbuild<K, Map>;
-    set_smem_once(kern, sm);
     unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms);
     grid = std::max<unsigned>(grid, (p.nbins + kMaxBinsPerCta - 1) / kMaxBinsPerCta);
-    {
-      HG_TRACE("k_binbuild", st);
+    HG_TRACE("k_binbuild", st);
+    if (p.tpb == 512) {
+      auto kern = k_binbuild<K, Map, 16>;
+      set_smem_once(kern, sm);
+      kern<<<grid, 512, sm, st>>>(ba, map);
+    } else {
+      auto kern = k_binbuild<K, Map, kBinNW>;
+      set_smem_once(kern, sm);
       kern<<<grid, kBinNW * 32, sm, st>>>(ba, map);
     }
   }
@@ -1182,7 +1194,8 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
   }
-  hg_status rc = probe_launch<K, Map>(qk, q, t->d_offsets, (const K*)t->d_keys, qc, V, st, map);
+  hg_status rc = probe_launch<K, Map>(qk, q, t->d_offsets, (const K*)t->d_keys, qc, V, st, map,
+                                      Map::kNeedsPos ? qi : nullptr);
   if (rc != HG_OK) return rc;
   {
     const uint64_t tiles = (q + kUnpermuteTile - 1) / kUnpermuteTile;
@@ -1200,12 +1213,14 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
 // pipeline, with the "bucket" of a key being one of its bytes.
 // ===========================================================================
 struct RadixByteMap {
+  static constexpr bool kNeedsPos = false;
   uint32_t shift;
   __device__ __forceinline__ void init() {}
   template <typename K>
-  __device__ __forceinline__ uint32_t operator()(K key) const {
+  __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
     return (uint32_t)(((uint64_t)key >> shift) & 255u);
   }
+  __device__ __forceinline__ uint32_t out_id(uint32_t id) const { return id; }
 };
 
 static void radix_layout(uint64_t n, uint64_t* chunk, uint32_t* G, size_t* o) {
@@ -1296,7 +1311,7 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
 // Explicit instantiations used by hg_api.cu (build entry point).
 #define HG_INST(K, M)                                                                                   \
   template hg_status build_v2<K, M>(const Plan&, const K*, const uint32_t*, uint32_t*, K*, uint32_t*, \
-                                    uint8_t*, cudaStream_t, M);                                         \
+                                    uint8_t*, cudaStream_t, M, uint32_t);                               \
   template hg_status build_v1<K, M>(uint64_t, uint64_t, const K*, const uint32_t*, uint32_t*, K*,       \
                                     uint32_t*, uint8_t*, cudaStream_t, M);                              \
   template hg_status probe_binned_impl<K, M>(const ProbePlan&, uint64_t, const hg_table*, const K*,     \
@@ -1306,5 +1321,12 @@ HG_INST(uint64_t, MurmurMap)
 HG_INST(uint32_t, LearnedMap)
 HG_INST(uint64_t, LearnedMap)
 #undef HG_INST
+// batched tables: V2 build and binned probe only (the map needs positions)
+template hg_status build_v2<uint32_t, BatchedMap>(const Plan&, const uint32_t*, const uint32_t*, uint32_t*,
+                                                  uint32_t*, uint32_t*, uint8_t*, cudaStream_t, BatchedMap,
+                                                  uint32_t);
+template hg_status probe_binned_impl<uint32_t, BatchedMap>(const ProbePlan&, uint64_t, const hg_table*,
+                                                           const uint32_t*, uint64_t, uint32_t*, uint8_t*,
+                                                           cudaStream_t, BatchedMap);
 
 }  // namespace hg

@@ -50,6 +50,7 @@ struct Plan {
   uint32_t G;        // input chunks of pass A
   uint64_t chunk;    // elements per chunk (multiple of 16)
   uint32_t emax;     // largest bin built in shared memory
+  uint32_t tpb;      // threads per bin-build CTA (512 or 1024)
   size_t o_H, o_C, o_CT, o_T, o_BS, o_ovf, o_bk, o_bi, total;
 };
 
@@ -72,9 +73,11 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
                             uint32_t* counts, uint8_t* ws, cudaStream_t st, Map map);
 size_t v1_workspace_bytes(int kb, uint64_t n, uint64_t V);
 
+// pos_base is added to every CSR offset written (the position of element 0
+// of these CSR arrays inside larger ones; 0 for a standalone table).
 template <typename K, typename Map>
 hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
-                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map);
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map, uint32_t pos_base = 0);
 template <typename K, typename Map>
 hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, uint32_t* offsets,
                    K* csr_k, uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map);

@@ -60,14 +60,65 @@ struct FastMod {
   }
 };
 
+// Bucket maps: operator()(key, pos) gives the bucket of the key at input
+// position pos (plain maps ignore the position; the batched map finds the
+// key's table from it); out_id(pos) is the id stored for the element whose
+// carried id is pos (plain maps store it unchanged).
 // Eq. 1: bucket = hash(key) mod V.
 struct MurmurMap {
+  static constexpr bool kNeedsPos = false;
   uint32_t seed;
   FastMod mod;
   __device__ __forceinline__ void init() {}
   template <typename K>
-  __device__ __forceinline__ uint32_t operator()(K key) const {
+  __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
     return mod(murmur3(key, seed));
+  }
+  __device__ __forceinline__ uint32_t out_id(uint32_t id) const { return id; }
+};
+
+// Batched tables (not in the paper): many tables share one bucket space.
+// Table t owns the global buckets [base_t, base_t + V_t] and the input
+// positions [begin_t, begin_{t+1}), of which the first len_t hold its keys
+// and the rest (fewer than 4) only align the next table to 16 bytes.  The
+// bucket of the key at position p is base_t + murmur3(key) mod V_t (Eq. 1
+// per table) for the table t holding p; an alignment position goes to the
+// spare bucket base_t + V_t, which no hash reaches, so table t's V_t + 1
+// offsets and its edges are exactly those of a standalone build.  t is found
+// through a page directory (the table holding the first position of every
+// page of 2^page_shift positions) and a short forward walk.  One instance
+// serves one launch sequence that sees the positions pos_base + [0, n) and
+// the buckets bucket_base + [0, V).
+struct BatchedMap {
+  static constexpr bool kNeedsPos = true;
+  uint32_t seed;
+  uint32_t page_shift;
+  uint64_t pos_base;
+  uint32_t bucket_base;
+  const uint64_t* begin;  // [T+1] first position of each table
+  const uint32_t* len;    // [T] positions of each table that hold keys
+  const uint32_t* page;   // table holding position (p << page_shift)
+  const uint4* desc;      // per table: {global bucket base, V_t, fastmod M low, M high}
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ uint32_t table_of(uint64_t p) const {
+    uint32_t t = __ldg(page + (p >> page_shift));
+    while (__ldg((const unsigned long long*)begin + t + 1) <= p) ++t;
+    return t;
+  }
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K key, uint32_t pos) const {
+    const uint64_t p = pos_base + pos;
+    const uint32_t t = table_of(p);
+    const uint4 d = __ldg(desc + t);
+    if (p - __ldg((const unsigned long long*)begin + t) >= __ldg(len + t)) return d.x - bucket_base + d.y;
+    const uint64_t M = ((uint64_t)d.w << 32) | d.z;
+    const uint32_t local = (uint32_t)__umul64hi(M * (uint64_t)murmur3(key, seed), (uint64_t)d.y);
+    return d.x - bucket_base + local;
+  }
+  // ids are stored table-local: position minus the table's first position
+  __device__ __forceinline__ uint32_t out_id(uint32_t pos) const {
+    const uint64_t p = pos_base + pos;
+    return (uint32_t)(p - __ldg((const unsigned long long*)begin + table_of(p)));
   }
 };
 
@@ -101,6 +152,7 @@ __device__ __forceinline__ float rmi_feature(uint64_t key) {
 }
 
 struct LearnedMap {
+  static constexpr bool kNeedsPos = false;
   const uint8_t* blob;  // device pointer
   uint64_t Vcap;        // buckets of the table being built (host-provided bound)
   float a, b;
@@ -121,8 +173,9 @@ struct LearnedMap {
     if (r >= __uint2float_rn(L)) return L - 1;
     return (uint32_t)r;
   }
+  __device__ __forceinline__ uint32_t out_id(uint32_t id) const { return id; }
   template <typename K>
-  __device__ __forceinline__ uint32_t operator()(K key) const {
+  __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
     const LearnedLeaf* lf = leaves + leaf_of(key);
     uint64_t xmin = __ldg((const unsigned long long*)&lf->xmin);
     float slope = __ldg(&lf->slope), icpt = __ldg(&lf->icpt);

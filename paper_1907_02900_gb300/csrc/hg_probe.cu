@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
                                                          const uint32_t* __restrict__ off,
                                                          const K* __restrict__ ck,
                                                          uint32_t* __restrict__ out, uint32_t nquads,
-                                                         Map map) {
+                                                         const uint32_t* __restrict__ qpos, Map map) {
   map.init();
   const uint64_t bd = blockDim.x;
   const uint64_t span = (uint64_t)gridDim.x * bd * QPT;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
       const uint64_t i = base + k * bd;
-      bq[k] = i < nq ? map(key[k]) : 0u;
+      bq[k] = i < nq ? map(key[k], qpos ? __ldg(qpos + i) : (uint32_t)i) : 0u;
       if ((bq[k] >> 2) < nquads) {
         o4[k] = __ldg(reinterpret_cast<const uint4*>(off) + (bq[k] >> 2));
       } else {  // quad not wholly inside the offsets array (or array not 16-byte aligned)
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
 
 template <typename K, typename Map>
 hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck, uint32_t* out,
-                       uint64_t V, cudaStream_t st, Map map) {
+                       uint64_t V, cudaStream_t st, Map map, const uint32_t* qpos) {
   if (nq == 0) return HG_OK;
   // quads of offsets wholly inside the V+1 entries (none if not 16-byte aligned)
   const uint32_t nquads = ((uintptr_t)off % 16 == 0) ? (uint32_t)((V + 1) / 4) : 0u;
@@ -85,18 +85,19 @@ hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck
   const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)sms * 16);
   {
     HG_TRACE("k_probe", st);
-    k_probe<K, Map, kProbeQPT><<<grid, kProbeThreads, 0, st>>>(q, nq, off, ck, out, nquads, map);
+    k_probe<K, Map, kProbeQPT><<<grid, kProbeThreads, 0, st>>>(q, nq, off, ck, out, nquads, qpos, map);
   }
   return last_launch_status();
 }
 
 #define HG_INST(K, M) \
   template hg_status probe_launch<K, M>(const K*, uint64_t, const uint32_t*, const K*, uint32_t*, uint64_t, \
-                                        cudaStream_t, M);
+                                        cudaStream_t, M, const uint32_t*);
 HG_INST(uint32_t, MurmurMap)
 HG_INST(uint64_t, MurmurMap)
 HG_INST(uint32_t, LearnedMap)
 HG_INST(uint64_t, LearnedMap)
+HG_INST(uint32_t, BatchedMap)
 #undef HG_INST
 
 }  // namespace hg

@@ -10,8 +10,10 @@ namespace hg {
 constexpr int kProbeThreads = 256;
 constexpr int kProbeQPT = 4;
 
+// qpos (optional): input position of each query, for maps that need it
+// (queries probed in a permuted order); null means query i is at position i.
 template <typename K, typename Map>
 hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck, uint32_t* out,
-                       uint64_t V, cudaStream_t st, Map map);
+                       uint64_t V, cudaStream_t st, Map map, const uint32_t* qpos = nullptr);
 
 }  // namespace hg

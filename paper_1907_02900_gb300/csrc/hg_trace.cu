@@ -35,6 +35,9 @@ bool prof_enabled() { return g_on; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t st) : name_(name), st_(st), a_(nullptr) {
   if (!g_on) return;
+  // launches recorded into a CUDA graph are timed as a whole by the caller
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   std::lock_guard<std::mutex> lk(g_mu);
   a_ = take_event();
   cudaEventRecord(a_, st_);

@@ -233,6 +233,66 @@ def batched_table_sizes(t: int, seed: int, lo_log2: float = 10.0, hi_log2: float
     return np.floor(np.exp2(lo_log2 + (hi_log2 - lo_log2) * u)).astype(np.int64)
 
 
+def batched_sizes(t: int, seed: int, total: int | None = None, lo_log2: float = 10.0,
+                  hi_log2: float = 22.0) -> np.ndarray:
+    """Sizes of t tables, log-uniform over [2**lo, 2**hi); with ``total`` they
+    are scaled by total / sum and floored (each at least 1), so the batch holds
+    at most ``total`` keys and keeps the log-uniform shape."""
+    n = batched_table_sizes(t, seed, lo_log2, hi_log2)
+    if total is not None:
+        n = np.maximum(1, np.floor(n * (total / float(n.sum())))).astype(np.int64)
+        excess = int(n.sum()) - total          # only from the floor of 1, a few keys at most
+        if excess > 0:
+            n[int(np.argmax(n))] -= excess
+    return n
+
+
+def batched_keys_u32(sizes: np.ndarray, seed: int) -> np.ndarray:
+    """Keys of all tables back to back: one uniform u32 stream, table t owns
+    the slice [sum(sizes[:t]), sum(sizes[:t+1]))."""
+    return uniform_keys_u32(int(np.sum(sizes)), seed)
+
+
+def batched_queries_u32(qsizes: np.ndarray, keys: np.ndarray, sizes: np.ndarray, hit_rate: float,
+                        seed: int) -> np.ndarray:
+    """Queries of all tables back to back.  Query j belongs to table t(j); a
+    fraction ``hit_rate`` are copies of a uniformly chosen key of that table
+    (none if it is empty), the rest are guaranteed misses."""
+    qsizes = np.asarray(qsizes, dtype=np.int64)
+    sizes = np.asarray(sizes, dtype=np.int64)
+    qtot = int(qsizes.sum())
+    kbeg = np.concatenate([[0], np.cumsum(sizes)])
+    qbeg = np.concatenate([[0], np.cumsum(qsizes)])
+    idx = np.arange(qtot, dtype=np.uint64)
+    t = np.searchsorted(qbeg, np.arange(qtot, dtype=np.int64), side="right") - 1
+    nt = sizes[t].astype(np.uint64)
+    thr = U64(int(round(hit_rate * (1 << 53))))
+    hit = ((splitmix64(seed, STREAM_QUERY_HIT, idx) >> U64(11)) < thr) & (nt > 0)
+    out = miss_keys_u32(idx, seed)
+    if hit.any():
+        x = splitmix64(seed, STREAM_QUERY_PICK, idx[hit])
+        with np.errstate(over="ignore"):
+            pick = ((x >> U64(32)) * nt[hit]) >> U64(32)
+        out[hit] = keys[(kbeg[t[hit]] + pick.astype(np.int64))]
+    return out
+
+
+def batched_table_queries_u32(q: int, start: int, table_keys: np.ndarray, hit_rate: float,
+                              seed: int) -> np.ndarray:
+    """The queries of one table of a batch: outputs start .. start+q-1 of the
+    batched query recipe (start = the table's first query in the unpadded
+    concatenation), hits drawn from ``table_keys``."""
+    idx = np.arange(start, start + q, dtype=np.uint64)
+    n = len(table_keys)
+    thr = U64(int(round(hit_rate * (1 << 53))))
+    hit = ((splitmix64(seed, STREAM_QUERY_HIT, idx) >> U64(11)) < thr) & (n > 0)
+    out = miss_keys_u32(idx, seed)
+    if hit.any():
+        pick = pick_below(splitmix64(seed, STREAM_QUERY_PICK, idx[hit]), n)
+        out[hit] = table_keys[pick.astype(np.int64)]
+    return out
+
+
 # Seeds of the five measured workloads.
 SEED_PLAIN = 0x48470001
 SEED_SCALE = 0x48470002

@@ -60,3 +60,28 @@ def test_batched_sizes_log_uniform():
     assert s.min() >= 1024 and s.max() < 1 << 22
     lg = np.log2(s)
     assert abs(lg.mean() - 16.0) < 0.15
+
+
+def test_batched_recipes_agree_table_by_table():
+    sizes = dg.batched_sizes(40, 3, lo_log2=0.0, hi_log2=10.0)
+    sizes[:3] = [0, 1, 5]
+    keys = dg.batched_keys_u32(sizes, 8)
+    q = dg.batched_queries_u32(sizes, keys, sizes, 0.5, 9)
+    ub = np.concatenate([[0], np.cumsum(sizes)])
+    for t in range(len(sizes)):
+        kt = dg.uniform_keys_u32(int(sizes[t]), 8, start=int(ub[t]))
+        assert np.array_equal(keys[ub[t]:ub[t + 1]], kt)
+        qt = dg.batched_table_queries_u32(int(sizes[t]), int(ub[t]), kt, 0.5, 9)
+        assert np.array_equal(q[ub[t]:ub[t + 1]], qt)
+    # about half the queries are keys of their own table
+    assert 0.4 < np.mean(np.isin(q, keys)) < 0.6
+
+
+def test_batched_sizes_total_and_shape():
+    n = dg.batched_sizes(10_000, dg.SEED_BATCH, total=(1 << 30) - 40_000)
+    assert n.sum() <= (1 << 30) - 40_000 and n.sum() > (1 << 30) - 50_000 and n.min() >= 1
+    raw = dg.batched_table_sizes(10_000, dg.SEED_BATCH)
+    assert raw.min() >= 1 << 10 and raw.max() < 1 << 22
+    # log-uniform: log2 sizes spread evenly over [10, 22)
+    h, _ = np.histogram(np.log2(raw), bins=12, range=(10, 22))
+    assert h.min() > 700 and h.max() < 980
