@@ -1,15 +1,26 @@
 #!/usr/bin/env python
-"""HashGraph benchmark on GB300: build (V2) + probe throughput at 2^28 keys.
+"""HashGraph benchmark on GB300.
 
-One step = one pass of the hot path over one batch of synthetic input:
-HashGraph-V2 build of N = 2^28 uint32 keys into V = 2^28 buckets (load
-factor 1), then HashGraph-Probe-Standard of Q = 2^28 queries (50% hits).
-value = (N + Q) / step time, in Gkeys/s, summed over ranks (each rank builds
-and probes its own independent table: weak scaling, no collective in the data
-path).  Inputs (1 GiB of keys, 1 GiB of queries) exceed the 129 MB L2, so no
-flush is needed between steps.
+Default workload (the headline line): one step = the whole hot path over one
+batch of synthetic input, HashGraph-V2 build (Alg. 2) of N = 2^28 uniform
+uint32 keys into V = 2^28 buckets (load factor 1), then the binned probe
+(HashGraph-Probe-Standard semantics, queries grouped by bucket range so every
+group probes an L2-resident slice of the table) of Q = 2^28 queries at 50%
+hits.  value = (N + Q) / step time in Gkeys/s, summed over ranks (each rank
+builds and probes its own table: weak scaling, no collective).  Inputs (2 GiB
+per step) exceed the 129 MB L2, so no flush is needed between steps.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Other workloads (one JSON line each, same keys), chosen by --workload:
+  plain    2^20 keys, 2^20 buckets, 2^20 queries (the oracle-sized case)
+  join     Alg. 3: build 2^27 uint64 Zipf(1) keys over 2^24 values and 2^27
+           uniform keys over the same values, join count and materialise
+  batched  10,000 tables, log-uniform sizes scaled to a 2^30-key total, each
+           probed by as many queries (50% hits), one graph launch per step
+           (autotuned); compared with a host loop of plain calls
+  learned  2^27 uint64 lognormal-mixture keys, learned bucket map (trained
+           once, on the GPU) vs Murmur: build + binned probe of 2^27 queries
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 
 Prints ONE JSON line on rank 0.
 """
@@ -32,6 +43,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "HashGraph build & probe Gkeys/s at 2^28 keys; % of HBM roofline"
 UNIT = "Gkeys/s"
+WORKLOADS = ("scale", "plain", "join", "batched", "learned")
 
 
 def parse():
@@ -40,14 +52,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hg", "reference"], default="hg")
-    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--workload", choices=WORKLOADS, default="scale")
+    ap.add_argument("--log2n", type=int, default=None)
     ap.add_argument("--log2v", type=int, default=None)
     ap.add_argument("--hit", type=float, default=0.5)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--standard-probe", action="store_true", help="time HashGraph-Probe-Standard instead of the binned probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
-    return ap.parse_args()
+    ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed runs of the per-table loop")
+    a = ap.parse_args()
+    if a.log2n is None:
+        a.log2n = 20 if a.workload == "plain" else 28
+    return a
 
 
 # --------------------------------------------------------------------------
@@ -130,9 +147,10 @@ def src_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, n: int, V: int):
+def recorded_traffic(kernel: str, units: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    to this workload; None when absent or taken on other kernel sources."""
+    by the units (keys or queries) one launch processes; None when absent or
+    taken on other kernel sources."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -141,42 +159,151 @@ def recorded_traffic(kernel: str, n: int, V: int):
     e = t.get(kernel)
     if not e or e.get("src_digest") != src_digest():
         return None
-    return e["bytes_per_key"] * n
+    return int(e["bytes_per_unit"] * units)
 
 
 # --------------------------------------------------------------------------
-# algorithmic bytes of each kernel (per launch) for the uint32 workload
+# algorithmic bytes of each kernel per launch (element granularity: every
+# input read once, every output written once)
 # --------------------------------------------------------------------------
 PROBE_KERNELS = {"k_hist_Q", "k_colscan_Q", "k_scan_Q", "k_partition_Q", "k_probe", "k_unpermute"}
 
 
-def algorithmic_bytes(kb: int, n: int, V: int, q: int, hit: float, binned: bool = True) -> dict:
-    """Bytes each kernel must move per launch (reads + writes of its inputs and
-    outputs at element granularity; the standard probe at 32-byte-sector
-    granularity for its random reads)."""
-    alpha = n / V
-    nonempty = hit + (1.0 - hit) * (1.0 - math.exp(-alpha))
-    table = 4 * (V + 1) + kb * n
-    out = {
+def algo_build(kb: int, n: int, V: int) -> dict:
+    return {
         "k_hist": kb * n,                                  # read keys
         "k_partition_A": kb * n + (kb + 4) * n,            # read keys, write (key, id)
         "k_partition_B": 2 * (kb + 4) * n,                 # read and write (key, id)
         "k_binbuild": 2 * (kb + 4) * n + 4 * V,            # read (key, id), write CSR + offsets
     }
+
+
+def algo_probe(kb: int, n: int, V: int, q: int, hit: float, binned: bool = True, positions: bool = False) -> dict:
+    """positions: the probe also reads each grouped query's position (batched
+    tables, whose bucket map needs it)."""
+    table = 4 * (V + 1) + kb * n
     if binned:
-        out.update({
+        return {
             "k_hist_Q": kb * q,                            # read queries
             "k_partition_Q": kb * q + (kb + 4) * q,        # read queries, write (query, position)
-            "k_probe": kb * q + 4 * q + table,             # read grouped queries, write counts, table once
+            "k_probe": kb * q + 4 * q + (4 * q if positions else 0) + table,  # grouped queries, counts, table once
             "k_unpermute": 3 * 4 * q,                      # read (position, count), write counts
-        })
-    else:
-        out["k_probe"] = q * (kb + 4) + q * 32 + q * 32 * nonempty  # 32 B sectors: offsets, first key
-    return out
+        }
+    alpha = n / V
+    nonempty = hit + (1.0 - hit) * (1.0 - math.exp(-alpha))
+    return {"k_probe": q * (kb + 4) + q * 32 + q * 32 * nonempty}  # 32 B sectors: offsets, first key
+
+
+def algo_join(kb: int, nA: int, nB: int, V: int, M: int) -> dict:
+    return {
+        "k_join_elem": kb * nA + kb * nB + 8 * (V + 1) + 8 * nA,          # both key arrays, both offsets, m out
+        "k_join_write": (kb + 4) * (nA + nB) + 4 * (V + 1) + 8 * nA + 16 * M,  # keys + ids, offsets, m, pairs
+        "k_join_bucket": 4 * (V + 1) + 8 * nA + 8 * V,
+    }
+
+
+def roofline(prof: dict, algo: dict, steps: int, elapsed_ms: float, hbm: float, peak_src: str, units: dict):
+    """Per-kernel rates from the live CUDA-event profile.  algo and units are
+    per step (all launches of the kernel in one step); achieved = bytes moved
+    over the kernel's total time, i.e. per launch on average."""
+    phases = {}
+    for k, (ms, c) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        e = {"avg_ms": round(ms / max(c, 1), 4), "launches": c, "share": round(ms / max(elapsed_ms, 1e-9), 4)}
+        if k in algo:
+            gbs = algo[k] * steps / (ms * 1e-3) / 1e9
+            e.update({"algo_bytes_per_launch": int(algo[k] * steps / max(c, 1)), "gbs": round(gbs, 1),
+                      "frac": round(gbs / hbm, 4)})
+        phases[k] = e
+    cand = [k for k in prof if k in algo]
+    if not cand:
+        return None, phases
+    dom = max(cand, key=lambda k: prof[k][0])
+    ms, c = prof[dom]
+    ach = algo[dom] * steps / (ms * 1e-3) / 1e9
+    per_launch_units = units.get(dom, 0) * steps / max(c, 1)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(ach / hbm, 4), "traffic": recorded_traffic(dom, per_launch_units),
+            "peak_source": f"hbm_gbs of {peak_src}"}
+    return roof, phases
+
+
+# --------------------------------------------------------------------------
+class Ctx:
+    """Device, ranks and the timed-region helper shared by every workload."""
+
+    def __init__(self, args):
+        import torch
+        import paper_1907_02900_gb300 as hg
+        self.torch, self.hg, self.args = torch, hg, args
+        self.world, self.rank, self.local = dist_info()
+        if self.world > 1:
+            import torch.distributed as dist
+            torch.cuda.set_device(self.local)
+            dist.init_process_group("nccl")
+        else:
+            torch.cuda.set_device(0)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        from paper_1907_02900_gb300 import _build
+        _build.build()
+        hg.load()
+        self.stream = torch.cuda.current_stream()
+        peaks, src = measured_peaks()
+        self.hbm, self.peak_src = float(peaks.get("hbm_gbs", 6800.0)), src
+
+    def barrier(self):
+        if self.world > 1:
+            self.torch.distributed.barrier()
+
+    def max_over_ranks(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        t = self.torch.tensor([x], device=self.dev, dtype=self.torch.float64)
+        self.torch.distributed.all_reduce(t, op=self.torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(self, fn, steps: int, profile: bool = True):
+        """Run fn() `steps` times between CUDA events (barrier + sync on both
+        sides); returns (max-over-ranks ms, clocks, per-kernel profile)."""
+        torch, hg = self.torch, self.hg
+        sampler = ClockSampler(self.local) if self.rank == 0 else None
+        hg.profile_reset()
+        hg.profile_enable(profile)
+        self.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        for _ in range(steps):
+            fn()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        self.barrier()
+        clocks = sampler.stop() if sampler else None
+        hg.profile_enable(False)
+        prof = hg.profile_read() if profile else {}
+        hg.profile_reset()
+        return self.max_over_ranks(e0.elapsed_time(e1)), clocks, prof
+
+    def line(self, workload: str, value: float, ms_per_step: float, dtype: str, config: dict, **extra) -> dict:
+        a = self.args
+        d = {"metric": METRIC if workload == "scale" else f"{workload}: build & probe Gkeys/s", "value": round(value, 3),
+             "unit": UNIT, "n_gpus": self.world, "steps": a.steps, "warmup": a.warmup,
+             "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+             "dtype": dtype, "data": "synthetic", "config": config}
+        d.update(extra)
+        d["gpu"] = self.torch.cuda.get_device_name(self.dev)
+        return d
+
+    def check_ws(self, ws, where: str):
+        st = self.hg.workspace_status(ws)
+        if st != 0:
+            raise RuntimeError(f"{where}: device status {self.hg.STATUS_NAMES.get(st, st)}")
 
 
 def oracle_sample(log2n: int, log2v: int, hit: float, seed: int):
-    """Oracle (single-threaded CPU) build + probe of a bounded sample; returns seconds."""
+    """Oracle (single-threaded CPU) build + probe of a bounded sample; returns (seconds, keys)."""
     import oracle
     from paper_1907_02900_gb300 import datagen as dg
     n = 1 << log2n
@@ -190,13 +317,18 @@ def oracle_sample(log2n: int, log2v: int, hit: float, seed: int):
     return time.perf_counter() - t0, 2 * n
 
 
+def cpu_line(secs: float, units: float, sample: str) -> dict:
+    return {"value": units / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample}, {secs:.1f} s single-threaded; nproc={os.cpu_count()}"}
+
+
 # --------------------------------------------------------------------------
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return
     log2v_full = args.log2v if args.log2v is not None else args.log2n
-    ln = args.cpu_log2n
+    ln = min(args.cpu_log2n, args.log2n)
     lv = ln + (log2v_full - args.log2n)
     for _ in range(max(args.warmup, 0) and 1):
         oracle_sample(ln - 4, lv - 4, args.hit, 7)
@@ -220,188 +352,334 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_hg(args):
-    import torch
-    import paper_1907_02900_gb300 as hg
+# --------------------------------------------------------------------------
+def run_scale(c: Ctx):
+    """Build + probe of one table (the headline; also the 2^20 'plain' case)."""
+    torch, hg, args = c.torch, c.hg, c.args
     from paper_1907_02900_gb300 import datagen as dg
-
-    world, rank, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
-    from paper_1907_02900_gb300 import _build
-    _build.build()
-    hg.load()
-
     n = 1 << args.log2n
     log2v = args.log2v if args.log2v is not None else args.log2n
     V = 1 << log2v
     q = n
-    seed = dg.SEED_SCALE + 1000 * rank
+    seed = dg.SEED_SCALE + 1000 * c.rank
     keys_h = dg.uniform_keys_u32(n, seed)
     q_h = dg.queries_u32(q, keys_h, args.hit, seed + 1)
-
-    def pinned(a):
-        t = torch.from_numpy(a.view(np.int32)).pin_memory()
-        return t
-
-    keys_p, q_p = pinned(keys_h), pinned(q_h)
+    keys_p = torch.from_numpy(keys_h.view(np.int32)).pin_memory()
+    q_p = torch.from_numpy(q_h.view(np.int32)).pin_memory()
     del keys_h, q_h
-    keys_d = keys_p.to(dev).view(torch.uint32)
-    q_d = q_p.to(dev).view(torch.uint32)
+    keys_d = keys_p.to(c.dev).view(torch.uint32)
+    q_d = q_p.to(c.dev).view(torch.uint32)
     cfg = hg.make_config(hg.KEY_U32, V, 0, "v2")
-    ws_bytes = hg.build_workspace_size(cfg, n)
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    offsets = torch.empty(V + 1, dtype=torch.uint32, device=dev)
-    ck = torch.empty(n, dtype=torch.uint32, device=dev)
-    ci = torch.empty(n, dtype=torch.uint32, device=dev)
-    counts = torch.empty(q, dtype=torch.uint32, device=dev)
+    ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=c.dev)
+    offsets = torch.empty(V + 1, dtype=torch.uint32, device=c.dev)
+    ck = torch.empty(n, dtype=torch.uint32, device=c.dev)
+    ci = torch.empty(n, dtype=torch.uint32, device=c.dev)
+    counts = torch.empty(q, dtype=torch.uint32, device=c.dev)
     table = hg.Table(offsets, ck, ci, cfg)
-    stream = torch.cuda.current_stream()
     binned = not args.standard_probe
-    pws = torch.empty(max(hg.probe_workspace_size(table, q), 1), dtype=torch.uint8, device=dev) if binned else None
+    pws = torch.empty(max(hg.probe_workspace_size(table, q), 1), dtype=torch.uint8, device=c.dev) if binned else None
 
     def step(kd, qd):
-        hg.build_into(cfg, kd, None, offsets, ck, ci, ws, stream)
+        hg.build_into(cfg, kd, None, offsets, ck, ci, ws, c.stream)
         if binned:
-            hg.probe_binned_into(table, qd, counts, pws, stream)
+            hg.probe_binned_into(table, qd, counts, pws, c.stream)
         else:
-            hg.probe_into(table, qd, counts, stream)
+            hg.probe_into(table, qd, counts, c.stream)
 
     for _ in range(args.warmup):
         step(keys_d, q_d)
     torch.cuda.synchronize()
-    st = hg.workspace_status(ws)
-    if st != 0:
-        raise RuntimeError(f"device status after warm-up: {hg.STATUS_NAMES.get(st, st)}")
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    sampler = ClockSampler(local) if rank == 0 else None
-    hg.profile_reset()
-    hg.profile_enable(True)
-    barrier()
-    torch.cuda.synchronize()
-    if sampler:
-        sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step(keys_d, q_d)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop() if sampler else None
-    hg.profile_enable(False)
-    prof = hg.profile_read()
-    hg.profile_reset()
-    elapsed_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    c.check_ws(ws, "build")
+    if binned:
+        c.check_ws(pws, "probe")
+    elapsed_ms, clocks, prof = c.timed(lambda: step(keys_d, q_d), args.steps)
     ms_per_step = elapsed_ms / args.steps
-    value = world * (n + q) * args.steps / (elapsed_ms * 1e-3) / 1e9
-    launches = sum(c for _, c in prof.values())
-
-    # per-kernel breakdown and the dominant kernel's roofline
-    peaks, peak_src = measured_peaks()
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    algo = algorithmic_bytes(4, n, V, q, args.hit, binned)
-    phases = {}
-    for k, (ms, c) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
-        avg = ms / max(c, 1)
-        e = {"avg_ms": round(avg, 4), "launches": c, "share": round(ms / max(elapsed_ms, 1e-9), 4)}
-        if k in algo:
-            gbs = algo[k] / (avg * 1e-3) / 1e9
-            e.update({"algo_bytes": int(algo[k]), "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)})
-        phases[k] = e
-    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
-    roof = None
-    if dom:
-        avg = prof[dom][0] / prof[dom][1]
-        b = algo.get(dom)
-        ach = b / (avg * 1e-3) / 1e9 if b else None
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1) if ach else None, "peak": hbm,
-                "unit": "GB/s", "frac": round(ach / hbm, 4) if ach else None,
-                "traffic": recorded_traffic(dom, n, V), "peak_source": f"hbm_gbs of {peak_src}"}
+    value = c.world * (n + q) * args.steps / (elapsed_ms * 1e-3) / 1e9
+    algo = dict(algo_build(4, n, V), **algo_probe(4, n, V, q, args.hit, binned))
+    units = {k: (q if k in PROBE_KERNELS else n) for k in algo}
+    roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
     build_ms = sum(prof[k][0] for k in prof if k not in PROBE_KERNELS) / args.steps
     probe_ms = sum(prof[k][0] for k in prof if k in PROBE_KERNELS) / args.steps
 
-    # end to end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
         counts_h = torch.empty(q, dtype=torch.int32).pin_memory()
-        kd2 = torch.empty(n, dtype=torch.int32, device=dev)
-        qd2 = torch.empty(q, dtype=torch.int32, device=dev)
-        torch.cuda.synchronize()
-        barrier()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(args.e2e_steps):
+        kd2 = torch.empty(n, dtype=torch.int32, device=c.dev)
+        qd2 = torch.empty(q, dtype=torch.int32, device=c.dev)
+
+        def e2e_step():
             kd2.copy_(keys_p, non_blocking=True)
             qd2.copy_(q_p, non_blocking=True)
             step(kd2.view(torch.uint32), qd2.view(torch.uint32))
             counts_h.copy_(counts.view(torch.int32), non_blocking=True)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = a0.elapsed_time(a1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * (n + q) * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+
+        e2e_ms, _, _ = c.timed(e2e_step, args.e2e_steps, profile=False)
+        e2e = {"value": c.world * (n + q) * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * (n + q), "d2h_bytes_per_step": 4 * q}
         del kd2, qd2
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ln = args.cpu_log2n
+    if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:
+        ln = min(args.cpu_log2n, args.log2n)
         lv = ln + (log2v - args.log2n)
-        secs, keys_done = oracle_sample(ln, lv, args.hit, seed + 7)
-        cpu = {"value": keys_done / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"single-threaded oracle build of 2^{ln} uint32 keys into 2^{lv} buckets + probe of "
-                         f"2^{ln} queries ({int(args.hit * 100)}% hits), {secs:.1f} s; nproc={os.cpu_count()}"}
+        secs, done = oracle_sample(ln, lv, args.hit, seed + 7)
+        cpu = cpu_line(secs, done, f"oracle build of 2^{ln} uint32 keys into 2^{lv} buckets + probe of 2^{ln} "
+                                   f"queries ({int(args.hit * 100)}% hits)")
+    config = {"workload": f"HashGraph-V2 build of 2^{args.log2n} uniform uint32 keys (implicit ids) into 2^{log2v} "
+                          f"buckets (murmur3) + {'binned probe' if binned else 'Probe-Standard'} of 2^{args.log2n} "
+                          f"queries at {int(args.hit * 100)}% hits, per GPU",
+              "global_batch": c.world * (n + q),
+              "l2": "inputs (8 B per key and query) exceed L2; no flush" if n >= 1 << 24 else
+                    "inputs fit in L2 (small case); no flush",
+              "parallelism": f"replicas x{c.world} (independent tables per GPU)"}
+    # the whole step against its minimum traffic: keys read, CSR + offsets written,
+    # queries read, counts written, the table read once
+    min_bytes = 4 * n + 8 * n + 4 * (V + 1) + 4 * q + 4 * q + (4 * (V + 1) + 4 * n)
+    return c.line("scale" if args.workload == "scale" else args.workload, value, ms_per_step, "u32", config,
+                  build_gkeys_s=round(n / (build_ms * 1e-3) / 1e9, 3) if build_ms else None,
+                  probe_gkeys_s=round(q / (probe_ms * 1e-3) / 1e9, 3) if probe_ms else None,
+                  end_to_end_min_bytes_frac=round(min_bytes / (ms_per_step * 1e-3) / 1e9 / c.hbm, 4),
+                  probe="binned" if binned else "standard", roofline=roof, phases=phases, cpu_baseline=cpu,
+                  e2e=e2e, gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": f"HashGraph-V2 build of 2^{args.log2n} uniform uint32 keys (implicit ids) into "
-                                   f"2^{log2v} buckets (murmur3) + Probe-Standard of 2^{args.log2n} queries at "
-                                   f"{int(args.hit * 100)}% hits, per GPU",
-                       "global_batch": world * (n + q), "l2": "inputs (2 GiB per step) exceed L2; no flush",
-                       "parallelism": f"replicas x{world} (independent tables per GPU)"},
-            "build_gkeys_s": round(n / (build_ms * 1e-3) / 1e9, 3) if build_ms else None,
-            "probe_gkeys_s": round(q / (probe_ms * 1e-3) / 1e9, 3) if probe_ms else None,
-            # the whole step against its minimum traffic: build 4N read + 8N CSR + 4V offsets written,
-            # probe 4Q read + 4Q written + the table read once
-            "end_to_end_min_bytes_frac": round((16 * n + 4 * V + 8 * q + 4 * (V + 1) + 4 * n)
-                                               / (ms_per_step * 1e-3) / 1e9 / hbm, 4),
-            "probe": "binned" if binned else "standard",
-            "roofline": roof, "phases": phases, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clocks, "gpu": torch.cuda.get_device_name(dev),
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+
+def run_join(c: Ctx):
+    torch, hg, args = c.torch, c.hg, c.args
+    from paper_1907_02900_gb300 import datagen as dg
+    n = 1 << 27
+    distinct = 1 << 24
+    V = 1 << 27
+    seed = dg.SEED_JOIN + 1000 * c.rank
+    a_h = dg.zipf_keys_u64(n, distinct, seed, 1.0)
+    b_h = dg.uniform_domain_keys_u64(n, distinct, seed + 1)
+    a_d = torch.from_numpy(a_h.view(np.int64)).to(c.dev).view(torch.uint64)
+    b_d = torch.from_numpy(b_h.view(np.int64)).to(c.dev).view(torch.uint64)
+    cfg = hg.make_config(hg.KEY_U64, V, 0, "v2")
+    ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=c.dev)
+
+    def alloc_table():
+        return hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=c.dev),
+                        torch.empty(n, dtype=torch.uint64, device=c.dev),
+                        torch.empty(n, dtype=torch.uint32, device=c.dev), cfg)
+
+    tA, tB = alloc_table(), alloc_table()
+    jws = torch.empty(hg.join_workspace_size(cfg, n, n), dtype=torch.uint8, device=c.dev)
+    total = torch.empty(1, dtype=torch.int64, device=c.dev)
+    hg.build_into(cfg, a_d, None, tA.offsets, tA.keys, tA.ids, ws, c.stream)
+    hg.build_into(cfg, b_d, None, tB.offsets, tB.keys, tB.ids, ws, c.stream)
+    hg.join_count_into(tA, tB, total, None, jws, c.stream)
+    M = int(total.item())
+    out_a = torch.empty(max(M, 1), dtype=torch.int64, device=c.dev)
+    out_b = torch.empty(max(M, 1), dtype=torch.int64, device=c.dev)
+
+    def step():
+        hg.build_into(cfg, a_d, None, tA.offsets, tA.keys, tA.ids, ws, c.stream)
+        hg.build_into(cfg, b_d, None, tB.offsets, tB.keys, tB.ids, ws, c.stream)
+        hg.join_count_into(tA, tB, total, None, jws, c.stream)
+        hg.join_materialize_into(tA, tB, out_a, out_b, total, jws, c.stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    c.check_ws(ws, "build")
+    c.check_ws(jws, "join")
+    elapsed_ms, clocks, prof = c.timed(step, args.steps)
+    ms = elapsed_ms / args.steps
+    value = c.world * 2 * n / (ms * 1e-3) / 1e9
+    # two builds per step
+    algo = {k: 2 * v for k, v in algo_build(8, n, V).items()}
+    algo.update(algo_join(8, n, n, V, M))
+    algo["k_join_elem"] = 2 * algo["k_join_elem"]     # once for the count, once for the materialisation
+    units = {k: 2 * n if k in algo_build(8, 1, 1) or k == "k_join_elem" else n for k in algo}
+    roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
+    join_ms = sum(prof[k][0] for k in prof if k.startswith("k_join") or k.startswith("k_scan")) / args.steps
+    cpu = None
+    if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        m = 1 << 21
+        sa = dg.zipf_keys_u64(m, distinct >> 6, seed + 2, 1.0)
+        sb = dg.uniform_domain_keys_u64(m, distinct >> 6, seed + 3)
+        t0 = time.perf_counter()
+        offA, kA, iA = oracle.build(sa, m)
+        offB, kB, iB = oracle.build(sb, m)
+        oracle.join_count(offA, kA, offB, kB, m)
+        secs = time.perf_counter() - t0
+        cpu = cpu_line(secs, 2 * m, f"oracle builds of 2 x 2^21 uint64 keys (same shape, 2^18 distinct) + join count")
+    config = {"workload": "Alg. 3 join: build 2^27 uint64 Zipf(1.0) keys over 2^24 values and 2^27 uniform keys over "
+                          "the same values into 2^27 buckets each (V2), join count + materialise int64 pairs",
+              "global_batch": c.world * 2 * n, "l2": "inputs exceed L2; no flush",
+              "parallelism": f"replicas x{c.world}", "pairs": M}
+    return c.line("join", value, ms, "u64", config, pairs_per_s=round(c.world * M / (ms * 1e-3) / 1e9, 3),
+                  join_ms=round(join_ms, 3), roofline=roof, phases=phases, cpu_baseline=cpu, e2e=None,
+                  gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
+
+
+def run_batched(c: Ctx):
+    torch, hg, args = c.torch, c.hg, c.args
+    from paper_1907_02900_gb300 import datagen as dg
+    import paper_1907_02900_gb300.datagen_gpu as dgg
+    T = 10_000
+    sizes = dg.batched_sizes(T, dg.SEED_BATCH, total=(1 << 30) - 4 * T)
+    qsizes = sizes.copy()
+    plan = hg.BatchPlan(sizes, qsizes, seed=dg.SEED_BATCH)
+    b = plan.alloc(c.dev)
+    dgg.fill_batch(plan, b, key_seed=dg.SEED_BATCH + 1 + c.rank, query_seed=dg.SEED_BATCH + 2 + c.rank,
+                   hit_rate=args.hit)
+    t0 = time.perf_counter()
+    tuned = plan.autotune(b, reps=2)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        plan.run(b)
+    torch.cuda.synchronize()
+    c.check_ws(b["ws"], "batch")
+    units = int(sizes.sum() + qsizes.sum())
+    elapsed_ms, clocks, _ = c.timed(lambda: plan.run(b), args.steps, profile=False)
+    ms = elapsed_ms / args.steps
+    value = c.world * units / (ms * 1e-3) / 1e9
+    # per-kernel breakdown from one eager (uncaptured) run of the same sequence
+    eager_ms, _, prof = c.timed(lambda: plan.run_eager(b), 1)
+    n, q, V = int(plan.total_keys), int(plan.total_queries), int(plan.total_offsets - 1)
+    algo = dict(algo_build(4, n, V), **algo_probe(4, n, V, q, args.hit, True, positions=True))
+    algo_total = sum(algo.values())
+    kunits = {k: (q if k in PROBE_KERNELS else n) for k in algo}
+    roof_k, phases = roofline(prof, algo, 1, eager_ms, c.hbm, c.peak_src, kunits)
+    # per-kernel launch totals sum the waves; the whole graph against all kernels' bytes
+    ach = algo_total / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "whole batch (one graph launch)", "achieved": round(ach, 1), "peak": c.hbm,
+            "unit": "GB/s", "frac": round(ach / c.hbm, 4), "traffic": None, "peak_source": f"hbm_gbs of {c.peak_src}",
+            "dominant_kernel": roof_k}
+    plain_ms = None
+    if args.plain_steps > 0:
+        plan.run_plain(b)
+        torch.cuda.synchronize()
+        pm, _, _ = c.timed(lambda: plan.run_plain(b), args.plain_steps, profile=False)
+        plain_ms = pm / args.plain_steps
+        plan.run(b)
+    cpu = None
+    if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        ub = np.concatenate([[0], np.cumsum(sizes)])
+        rng = np.random.default_rng(1)
+        pick = rng.choice(T, 200, replace=False)
+        done, secs = 0, 0.0
+        for t in pick:
+            kt = dg.uniform_keys_u32(int(sizes[t]), dg.SEED_BATCH + 1, start=int(ub[t]))
+            qt = dg.batched_table_queries_u32(int(qsizes[t]), int(ub[t]), kt, args.hit, dg.SEED_BATCH + 2)
+            s0 = time.perf_counter()
+            off, ck, _ = oracle.build(kt, int(sizes[t]), seed=dg.SEED_BATCH)
+            oracle.probe(off, ck, qt, int(sizes[t]), seed=dg.SEED_BATCH)
+            secs += time.perf_counter() - s0
+            done += len(kt) + len(qt)
+        cpu = cpu_line(secs, done, f"oracle build + probe of 200 random tables of the batch ({done} keys+queries)")
+    config = {"workload": f"{T} tables, log-uniform sizes scaled to {int(sizes.sum())} uint32 keys in total "
+                          f"({int(sizes.min())}..{int(sizes.max())} per table), V_t = n_t, as many queries at "
+                          f"{int(args.hit * 100)}% hits; build + binned probe of every table, one CUDA graph launch",
+              "global_batch": c.world * units, "l2": "inputs exceed L2; no flush",
+              "parallelism": f"replicas x{c.world}", "autotuned": tuned, "autotune_s": round(tune_s, 2),
+              "waves": plan.config()["waves"]}
+    return c.line("batched", value, ms, "u32", config,
+                  plain_loop_gkeys_s=round(units / (plain_ms * 1e-3) / 1e9, 3) if plain_ms else None,
+                  speedup_vs_plain_loop=round(plain_ms / ms, 2) if plain_ms else None,
+                  roofline=roof, phases=phases, cpu_baseline=cpu, e2e=None,
+                  gpu_launches=sum(v[1] for v in prof.values()) * args.steps, clocks=clocks)
+
+
+def run_learned(c: Ctx):
+    torch, hg, args = c.torch, c.hg, c.args
+    from paper_1907_02900_gb300 import datagen as dg
+    n = 1 << 27
+    V = 1 << 27
+    q = n
+    seed = dg.SEED_LEARNED + 1000 * c.rank
+    keys_h = dg.lognormal_mixture_u64(n, seed)
+    q_h = dg.queries_u64(q, keys_h, args.hit, seed + 1)
+    keys_d = torch.from_numpy(keys_h.view(np.int64)).to(c.dev).view(torch.uint64)
+    q_d = torch.from_numpy(q_h.view(np.int64)).to(c.dev).view(torch.uint64)
+    del q_h
+    # training: once per key set, timed on its own
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(c.stream)
+    model, diag = hg.learned_train(keys_d, V)
+    t1.record(c.stream)
+    torch.cuda.synchronize()
+    train_ms = t0.elapsed_time(t1)
+    chosen, rep = hg.choose_map(keys_d, V, model)
+
+    def setup(mdl):
+        cfg = hg.make_config(hg.KEY_U64, V, 0, "v2", model=mdl)
+        ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=c.dev)
+        t = hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=c.dev),
+                     torch.empty(n, dtype=torch.uint64, device=c.dev),
+                     torch.empty(n, dtype=torch.uint32, device=c.dev), cfg, model=mdl)
+        pws = torch.empty(hg.probe_workspace_size(t, q), dtype=torch.uint8, device=c.dev)
+        counts = torch.empty(q, dtype=torch.uint32, device=c.dev)
+
+        def step():
+            hg.build_into(cfg, keys_d, None, t.offsets, t.keys, t.ids, ws, c.stream)
+            hg.probe_binned_into(t, q_d, counts, pws, c.stream)
+        return step, ws, pws, counts
+
+    res = {}
+    for name, mdl in (("learned", model), ("murmur", None)):
+        step, ws, pws, counts = setup(mdl)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        c.check_ws(ws, name)
+        c.check_ws(pws, name)
+        el, clocks, prof = c.timed(step, args.steps)
+        res[name] = (el, clocks, prof, counts.clone())
+        del ws, pws
+    same_counts = bool(torch.equal(res["learned"][3], res["murmur"][3]))
+    el, clocks, prof, _ = res["learned"]
+    ms = el / args.steps
+    value = c.world * (n + q) / (ms * 1e-3) / 1e9
+    murmur_value = c.world * (n + q) / (res["murmur"][0] / args.steps * 1e-3) / 1e9
+    algo = dict(algo_build(8, n, V), **algo_probe(8, n, V, q, args.hit, True))
+    units = {k: (q if k in PROBE_KERNELS else n) for k in algo}
+    roof, phases = roofline(prof, algo, args.steps, el, c.hbm, c.peak_src, units)
+    cpu = None
+    if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build_oracle()
+        m = 1 << 21
+        blob = model.cpu().numpy().view(np.uint8)
+        ks = keys_h[:m]
+        qs = dg.queries_u64(m, ks, args.hit, seed + 5)
+        s0 = time.perf_counter()
+        off, ck, _ = oracle.build(ks, V, model=blob)
+        oracle.probe(off, ck, qs, V, model=blob)
+        secs = time.perf_counter() - s0
+        cpu = cpu_line(secs, 2 * m, "oracle build + probe of 2^21 of the keys with the GPU-trained learned map")
+    config = {"workload": "2^27 uint64 keys, mixture of 64 lognormals (sigma 0.5..2) + 10% uniform, V = 2^27, "
+                          "learned piecewise-linear CDF map (1 root + 1024 leaves, trained on a 1% sample on the GPU) "
+                          "vs murmur3; V2 build + binned probe of 2^27 queries at 50% hits",
+              "global_batch": c.world * (n + q), "l2": "inputs exceed L2; no flush",
+              "parallelism": f"replicas x{c.world}"}
+    return c.line("learned", value, ms, "u64", config, murmur_gkeys_s=round(murmur_value, 3),
+                  learned_vs_murmur=round(value / murmur_value, 3), identical_counts=same_counts,
+                  train_ms=round(train_ms, 2), loss_before=diag["loss_before"], loss_after=diag["loss_after"],
+                  bucket_stats=rep, fallback_to_murmur=not rep["kept"], roofline=roof, phases=phases,
+                  cpu_baseline=cpu, e2e=None, gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
 
 
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
-        run_hg(args)
+        return
+    c = Ctx(args)
+    fn = {"scale": run_scale, "plain": run_scale, "join": run_join, "batched": run_batched,
+          "learned": run_learned}[args.workload]
+    line = fn(c)
+    if c.rank == 0:
+        print(json.dumps(line), flush=True)
+    if c.world > 1:
+        c.torch.distributed.destroy_process_group()
 
 
 if __name__ == "__main__":

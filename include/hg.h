@@ -222,6 +222,8 @@ hg_status hg_bucket_stats(const hg_config* cfg, const void* d_keys, uint64_t n, 
  *   the common bucket space.  The launch sequence is captured into a CUDA
  *   graph on the first call with a given set of buffers and configuration
  *   and replayed by later calls with the same ones.
+ * hg_batch_run_eager: the same launch sequence enqueued directly, without
+ *   a graph (per-kernel tracing and profiling see each launch).
  * hg_batch_autotune: synchronous; times `reps` runs of every candidate (bin
  *   shift near the automatic one x 512 / 1024 threads per bin) on the given
  *   buffers, keeps the fastest and returns its time.  Results do not depend
@@ -247,6 +249,9 @@ hg_status hg_batch_get_config(const hg_batch_plan* plan, uint32_t* bin_shift, ui
 hg_status hg_batch_run(hg_batch_plan* plan, const void* d_keys, const void* d_queries, uint32_t* d_offsets,
                        void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts, void* d_ws,
                        size_t ws_bytes, void* stream);
+hg_status hg_batch_run_eager(hg_batch_plan* plan, const void* d_keys, const void* d_queries,
+                             uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts,
+                             void* d_ws, size_t ws_bytes, void* stream);
 hg_status hg_batch_autotune(hg_batch_plan* plan, const void* d_keys, const void* d_queries,
                             uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts,
                             void* d_ws, size_t ws_bytes, void* stream, uint32_t reps, float* h_best_ms);

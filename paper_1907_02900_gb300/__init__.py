@@ -77,6 +77,7 @@ SIGNATURES = {
     "hg_batch_run": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_batch_autotune": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _U32, _VP]),
     "hg_batch_run_plain": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_batch_run_eager": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_static_scratch_bytes": (_SZ, []),
     "hg_build_static_scratch": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
@@ -336,6 +337,23 @@ def join_materialize(A: Table, B: Table, capacity: int | None = None, stream=Non
     return oa[:m], ob[:m]
 
 
+def join_count_into(A: Table, B: Table, total, bucket_counts, ws, stream=None):
+    """hg_join_count on caller-provided tensors (bucket_counts may be None)."""
+    _same_space(A, B)
+    ta, tb = A.view(), B.view()
+    _check(load().hg_join_count(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(total),
+                                _ptr(bucket_counts), _ptr(ws), ws.numel(), _stream_handle(stream)), "hg_join_count")
+
+
+def join_materialize_into(A: Table, B: Table, out_a, out_b, total, ws, stream=None):
+    """hg_join_materialize on caller-provided tensors; capacity = out_a.numel()."""
+    _same_space(A, B)
+    ta, tb = A.view(), B.view()
+    _check(load().hg_join_materialize(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(out_a),
+                                      _ptr(out_b), out_a.numel(), _ptr(total), _ptr(ws), ws.numel(),
+                                      _stream_handle(stream)), "hg_join_materialize")
+
+
 def workspace_status(ws, stream=None) -> int:
     return int(load().hg_workspace_status(_ptr(ws), _stream_handle(stream)))
 
@@ -517,6 +535,9 @@ class BatchPlan:
 
     def run(self, b: dict, stream=None):
         _check(self._lib.hg_batch_run(self._h, *self._args(b), _stream_handle(stream)), "hg_batch_run")
+
+    def run_eager(self, b: dict, stream=None):
+        _check(self._lib.hg_batch_run_eager(self._h, *self._args(b), _stream_handle(stream)), "hg_batch_run_eager")
 
     def run_plain(self, b: dict, stream=None):
         _check(self._lib.hg_batch_run_plain(self._h, *self._args(b), _stream_handle(stream)), "hg_batch_run_plain")

@@ -452,6 +452,17 @@ hg_status hg_batch_run(hg_batch_plan* P, const void* d_keys, const void* d_queri
   return run_graph(P, b, (cudaStream_t)stream);
 }
 
+hg_status hg_batch_run_eager(hg_batch_plan* P, const void* d_keys, const void* d_queries, uint32_t* d_offsets,
+                             void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts, void* d_ws, size_t ws_bytes,
+                             void* stream) {
+  if (!P) return HG_ERR_INVALID_ARG;
+  const Bufs b{(const uint32_t*)d_keys, (const uint32_t*)d_queries, d_offsets, (uint32_t*)d_csr_keys,
+               d_csr_ids, d_counts, (uint8_t*)d_ws};
+  const hg_status rc = check_bufs(P, b, ws_bytes);
+  if (rc != HG_OK) return rc;
+  return enqueue(P, b, (cudaStream_t)stream);
+}
+
 hg_status hg_batch_autotune(hg_batch_plan* P, const void* d_keys, const void* d_queries, uint32_t* d_offsets,
                             void* d_csr_keys, uint32_t* d_csr_ids, uint32_t* d_counts, void* d_ws, size_t ws_bytes,
                             void* stream, uint32_t reps, float* h_best_ms) {

@@ -1038,6 +1038,15 @@ hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, u
 // order by a merge over the groups (inside a group the query positions
 // ascend, because the partition is stable).
 // ===========================================================================
+// Counts back to query order when the positions inside every group come in
+// long ascending runs (batched tables: a table's queries fall into one or two
+// groups): a plain in-order scatter, coalesced along each run.
+__global__ void k_scatter_counts(const uint32_t* __restrict__ Qi, const uint32_t* __restrict__ Qc, uint64_t Q,
+                                 uint32_t* __restrict__ counts) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < Q; j += (uint64_t)gridDim.x * blockDim.x)
+    counts[__ldcs(Qi + j)] = __ldcs(Qc + j);
+}
+
 constexpr int kUnpermuteThreads = 1024;
 constexpr uint32_t kUnpermuteTile = 8192;
 constexpr int kUnpermuteGPW = 8;  // groups per warp: 256 groups / 32 warps
@@ -1114,10 +1123,12 @@ bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePl
   const DevInfo& di = dev_info();
   const int kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
   const uint64_t V = cfg->num_buckets;
-  const double table_bytes = 4.0 * (double)(V + 1) + (double)kb * (double)table_n;
-  int lng = 0;
-  while (lng < 8 && table_bytes / (double)(1u << lng) > (double)kProbeSliceBytes) ++lng;
-  int sg = ceil_log2_u64(V) - lng;
+  // 256 groups (fewer only for V < 256): a group's slice of the table stays
+  // well below L2 up to 4 GB tables (a 2^28-key table gives 8 MB slices), and
+  // with many groups every output tile of the merge draws on many of them,
+  // which keeps its warps evenly loaded.
+  (void)table_n;
+  int sg = ceil_log2_u64(V) - 8;
   if (sg < 0) sg = 0;
   p->sg = (uint32_t)sg;
   p->ng = (uint32_t)(((V - 1) >> sg) + 1);
@@ -1202,7 +1213,11 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)2 * di.sms));
     const uint64_t span = (q + grid - 1) / grid;
     HG_TRACE("k_unpermute", st);
-    k_unpermute<<<(unsigned)grid, kUnpermuteThreads, 0, st>>>(qi, qc, GS, p.ng, q, span, counts);
+    if (Map::kNeedsPos)
+      k_scatter_counts<<<(unsigned)std::min<uint64_t>((q + 255) / 256, (uint64_t)di.sms * 16), 256, 0, st>>>(
+          qi, qc, q, counts);
+    else
+      k_unpermute<<<(unsigned)grid, kUnpermuteThreads, 0, st>>>(qi, qc, GS, p.ng, q, span, counts);
   }
   return last_launch_status();
 }

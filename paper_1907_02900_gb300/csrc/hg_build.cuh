@@ -57,7 +57,6 @@ struct Plan {
 bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p);
 
 // Binned probe: query groups by bucket range, workspace layout.
-constexpr double kProbeSliceBytes = 16.0 * 1024 * 1024;  // table bytes per query group (L2-resident)
 struct ProbePlan {
   uint32_t sg;   // group = bucket >> sg
   uint32_t ng;   // groups (<= 256)
