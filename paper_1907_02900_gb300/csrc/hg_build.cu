@@ -48,10 +48,11 @@ size_t big_smem_bytes(int kb, uint32_t nb) {
   return align_up(b, 16) + (size_t)rank_words<kBinNW>() * 4 + 32 * 4 + 64;
 }
 
-size_t part_smem_bytes(int kb, bool ids_in, int ipt, bool item_list) {
-  const size_t tile = (size_t)kPartNW * 32 * ipt;
+size_t part_smem_bytes(int kb, bool ids_in, int ipt, bool item_list, int nw) {
+  const size_t tile = (size_t)nw * 32 * ipt;
   const size_t tb = tile + 16;
-  size_t b = 2 * tb * kb + (ids_in ? 2 * tb * 4 : 0) + tile * (kb + 4 + 1) + (size_t)rank_words<kPartNW>() * 4 +
+  const size_t rw = nw == kPartNW ? (size_t)rank_words<kPartNW>() : (size_t)rank_words<kPartBNW>();
+  size_t b = 2 * tb * kb + (ids_in ? 2 * tb * 4 : 0) + tile * (kb + 4 + 1) + rw * 4 +
              2 * 256 * 4;
   return align_up(b, 16) + (item_list ? 2 * kMaxItemsPerCta * 4 : 0) + 32 * 4 + 2 * 8 + 64;
 }
@@ -248,9 +249,8 @@ struct PartArgs {
   uint32_t* status;
 };
 
-template <typename K, typename Map, bool PASS_B, int IPT>
-__global__ void __launch_bounds__(kPartNW * 32, kPartMinBlocks) k_partition(PartArgs<K> a, Map map) {
-  constexpr int NW = kPartNW;
+template <typename K, typename Map, bool PASS_B, int IPT, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map map) {
   constexpr uint32_t TILE = NW * 32 * IPT;
   constexpr uint32_t TB = TILE + 16;
   const bool has_ids = PASS_B || a.in_i != nullptr;
@@ -892,8 +892,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.BS = BS;
   pa.status = status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, kPartIPT, false);
-    auto kern = k_partition<K, Map, false, kPartIPT>;
+    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, kPartIPT, false, kPartNW);
+    auto kern = k_partition<K, Map, false, kPartIPT, kPartNW, kPartMinBlocks>;
     set_smem_once(kern, sm);
     {
       HG_TRACE("k_partition_A", st);
@@ -906,11 +906,11 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     pb.in_i = csr_i;
     pb.out_k = bk;
     pb.out_i = bi;
-    const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true);
-    auto kern = k_partition<K, Map, true, kPartIPTB>;
+    const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true, kPartBNW);
+    auto kern = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks>;
     set_smem_once(kern, sm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPartNW * 32, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPartBNW * 32, sm);
     // ~32K edges per item: enough to amortise the per-item set-up
     const uint64_t per_chunk_sb = std::max<uint64_t>(1, p.n / ((uint64_t)p.G * p.nsb));
     pb.gg = (uint32_t)std::min<uint64_t>(p.G, std::max<uint64_t>(1, 32768 / per_chunk_sb));
@@ -920,7 +920,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     grid = (unsigned)std::max<uint64_t>(grid, (items + kMaxItemsPerCta - 1) / kMaxItemsPerCta);
     {
       HG_TRACE("k_partition_B", st);
-      kern<<<grid, kPartNW * 32, sm, st>>>(pb, map);
+      kern<<<grid, kPartBNW * 32, sm, st>>>(pb, map);
     }
   }
   BinArgs<K> ba{};
@@ -1199,8 +1199,8 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.BS = GS;
   pa.status = &hdr->status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), false, kPartIPT, false);
-    auto kern = k_partition<K, Map, false, kPartIPT>;
+    const size_t sm = part_smem_bytes(sizeof(K), false, kPartIPT, false, kPartNW);
+    auto kern = k_partition<K, Map, false, kPartIPT, kPartNW, kPartMinBlocks>;
     set_smem_once(kern, sm);
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
@@ -1279,8 +1279,8 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
   uint32_t* ids = (uint32_t*)(ws + o[6]);
   uint64_t* src = keys;
   uint64_t* dst = tmp;
-  const size_t psm = part_smem_bytes(8, false, kPartIPT, false);
-  auto kp = k_partition<uint64_t, RadixByteMap, false, kPartIPT>;
+  const size_t psm = part_smem_bytes(8, false, kPartIPT, false, kPartNW);
+  auto kp = k_partition<uint64_t, RadixByteMap, false, kPartIPT, kPartNW, kPartMinBlocks>;
   set_smem_once(kp, psm);
   auto kh = k_hist<uint64_t, RadixByteMap>;
   set_smem_once(kh, 1024);

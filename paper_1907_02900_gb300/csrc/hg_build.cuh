@@ -21,10 +21,18 @@ constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local ind
 #ifndef HG_PART_MINB
 #define HG_PART_MINB 2
 #endif
-constexpr int kPartNW = HG_PART_NW;      // warps of the partition kernels
+#ifndef HG_PARTB_NW
+#define HG_PARTB_NW 8
+#endif
+#ifndef HG_PARTB_MINB
+#define HG_PARTB_MINB 4
+#endif
+constexpr int kPartNW = HG_PART_NW;      // warps of the partition kernels (pass A, query grouping)
 constexpr int kPartIPT = HG_PART_IPT;    // items per thread, pass A
-constexpr int kPartIPTB = HG_PART_IPTB;  // items per thread, pass B (smaller tile: 2 CTAs per SM)
+constexpr int kPartIPTB = HG_PART_IPTB;  // items per thread, pass B
 constexpr int kPartMinBlocks = HG_PART_MINB;
+constexpr int kPartBNW = HG_PARTB_NW;    // pass B: smaller CTAs, more of them per SM
+constexpr int kPartBMinBlocks = HG_PARTB_MINB;
 constexpr uint32_t kMaxItemsPerCta = 128;  // pass B work items one CTA may own
 constexpr uint32_t kMaxBinsPerCta = 256;   // bins one bin-build CTA may own
 constexpr int kPartTile = kPartNW * 32 * kPartIPT;  // 4096 elements per tile

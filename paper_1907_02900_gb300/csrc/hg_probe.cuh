@@ -7,8 +7,15 @@
 
 namespace hg {
 
-constexpr int kProbeThreads = 256;
-constexpr int kProbeQPT = 4;
+// Probe geometry (compile-time; the defaults are the tuned values).
+#ifndef HG_PROBE_THREADS
+#define HG_PROBE_THREADS 256
+#endif
+#ifndef HG_PROBE_QPT
+#define HG_PROBE_QPT 1
+#endif
+constexpr int kProbeThreads = HG_PROBE_THREADS;
+constexpr int kProbeQPT = HG_PROBE_QPT;  // queries per thread with their loads in flight together
 
 // qpos (optional): input position of each query, for maps that need it
 // (queries probed in a permuted order); null means query i is at position i.
