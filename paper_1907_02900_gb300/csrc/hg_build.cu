@@ -37,16 +37,20 @@ static int ceil_log2_u64(uint64_t x) {
 
 size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf) {
   // staging buffers of keys and ids, lb and slot arrays (u16), packed u16
-  // bucket counters, heavy-bucket list
+  // bucket counters, heavy-bucket list, list of buckets with two or more edges
   size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + 2 * (size_t)emax * 2 + (((size_t)1 << s) + 1) / 2 * 4 +
-             ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2;
+             ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2 + ((size_t)emax / 2 + 2) * 2;
   return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
 }
 
-size_t big_smem_bytes(int kb, uint32_t nb) {
-  size_t b = align_up((size_t)nb * 4, 16) + (size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2;
-  return align_up(b, 16) + (size_t)rank_words<kBinNW>() * 4 + 32 * 4 + 64;
+// stream_runs' shared memory after the cursors: tile keys and ids, four u16
+// tile arrays, the ranking counters and a scan scratch (last 128 bytes)
+__host__ __device__ inline size_t big_rest_bytes(int kb) {
+  return align_up((size_t)kBigTile * (kb + 4) + 4 * (size_t)kBigTile * 2, 16) + (size_t)rank_words<kBinNW>() * 4 +
+         32 * 4;
 }
+
+size_t big_smem_bytes(int kb, uint32_t nb) { return align_up((size_t)nb * 4, 16) + big_rest_bytes(kb) + 64; }
 
 size_t part_smem_bytes(int kb, bool ids_in, int ipt, bool item_list, int nw) {
   const size_t tile = (size_t)nw * 32 * ipt;
@@ -96,6 +100,12 @@ bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
   p->o_T = o;   o = align_up(o + (size_t)p->nbins * 4);
   p->o_BS = o;  o = align_up(o + ((size_t)p->nbins + 1) * 4);
   p->o_ovf = o; o = align_up(o + (size_t)p->nbins * 4);
+  // a huge bin holds more than kHugeSeg edges, so there are at most n / kHugeSeg
+  // of them and their segments number at most 2 n / kHugeSeg
+  p->max_rows = (uint32_t)(2 * (n / kHugeSeg) + 2);
+  p->o_hlist = o;   o = align_up(o + (size_t)(n / kHugeSeg + 1) * 3 * 4);
+  p->o_rowdesc = o; o = align_up(o + (size_t)p->max_rows * 2 * 4);
+  p->o_rowcnt = o;  o = align_up(o + (size_t)p->max_rows * ((size_t)1 << p->s) * 4);
   p->o_bk = o;  o = align_up(o + ((size_t)n + 16) * p->kb);
   p->o_bi = o;  o = align_up(o + ((size_t)n + 16) * 4);
   p->total = o;
@@ -199,14 +209,26 @@ __global__ void k_colscan(uint32_t* __restrict__ tab, uint32_t rows, uint32_t co
   if (coltot) coltot[c] = run;
 }
 
+// Bins above kHugeSeg edges: list entries (bin, first row, rows) and one
+// row (bin, segment) per kHugeSeg-edge segment.  Null list: no such split.
+struct HugeArgs {
+  uint32_t* list;
+  uint32_t* count;
+  uint32_t* rows;
+  uint32_t* rowdesc;
+  uint32_t max_rows;
+  uint32_t* status;
+};
+
 // Exclusive scan of the bin totals (one CTA); list of bins too large for the
-// shared-memory bin build; closing CSR offset offsets[V] = n.
+// shared-memory bin build (huge ones split into segments); closing CSR
+// offset offsets[V] = n.
 __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__ T, uint32_t nbins,
                                                     uint32_t* __restrict__ BS, uint32_t emax,
                                                     uint32_t* __restrict__ ovf_list,
                                                     uint32_t* __restrict__ ovf_count,
                                                     uint32_t* __restrict__ offsets, uint64_t V,
-                                                    uint32_t n_end) {
+                                                    uint32_t n_end, HugeArgs h) {
   __shared__ uint32_t wsum[32];
   const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
   const uint32_t b = threadIdx.x * per, e = min(b + per, nbins);
@@ -217,7 +239,25 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
   for (uint32_t i = b; i < e; ++i) {
     BS[i] = base;
     base += T[i];
-    if (T[i] > emax) ovf_list[atomicAdd(ovf_count, 1u)] = i;
+    if (T[i] <= emax) continue;
+    if (h.list == nullptr || T[i] <= kHugeSeg) {
+      ovf_list[atomicAdd(ovf_count, 1u)] = i;
+      continue;
+    }
+    const uint32_t nr = (T[i] + kHugeSeg - 1) / kHugeSeg;
+    const uint32_t r0 = atomicAdd(h.rows, nr);
+    if (r0 + nr > h.max_rows) {  // cannot happen: the bound counts every huge bin
+      set_status(h.status, HG_ERR_OVERFLOW);
+      continue;
+    }
+    const uint32_t k = atomicAdd(h.count, 1u);
+    h.list[3 * k] = i;
+    h.list[3 * k + 1] = r0;
+    h.list[3 * k + 2] = nr;
+    for (uint32_t r = 0; r < nr; ++r) {
+      h.rowdesc[2 * (r0 + r)] = i;
+      h.rowdesc[2 * (r0 + r) + 1] = r;
+    }
   }
   if (threadIdx.x == 0) {
     BS[nbins] = total;
@@ -452,9 +492,11 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
   uint16_t* opos = (uint16_t*)sp; sp += (size_t)a.emax * 2;
   uint32_t* cnt = (uint32_t*)sp; sp += (((size_t)1 << a.s) + 1) / 2 * 4;
   uint16_t* heavy = (uint16_t*)sp; sp += (size_t)(a.emax / (kBinSmallBucket + 1) + 2) * 2;
+  uint16_t* multi = (uint16_t*)sp; sp += (size_t)(a.emax / 2 + 2) * 2;  // buckets holding >= 2 edges
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
-  uint32_t* nheavy = (uint32_t*)sp; sp += 16;
+  uint32_t* nheavy = (uint32_t*)sp; sp += 16;  // [0] heavy buckets, [1] entries of multi
+  uint32_t* nmulti = nheavy + 1;
   uint32_t* bl_start = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;  // this CTA's bins: start, size
   uint32_t* bl_size = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;
   uint64_t* bar = (uint64_t*)sp;
@@ -502,7 +544,10 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
     const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
     const uint32_t nwords = (nb + 1) >> 1;
     for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) cnt[w] = 0;
-    if (threadIdx.x == 0) *nheavy = 0;
+    if (threadIdx.x == 0) {
+      *nheavy = 0;
+      *nmulti = 0;
+    }
     const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
     if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
     const uint32_t E = bl_size[jb], start = bl_start[jb];
@@ -536,6 +581,8 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
         const uint32_t v = 2 * w;
         a.offsets[bucket0 + v] = a.pos_base + start + base;
         if (v + 1 < nb) a.offsets[bucket0 + v + 1] = a.pos_base + start + base + lo;
+        if (lo > 1) multi[atomicAdd(nmulti, 1u)] = (uint16_t)v;
+        if (hi > 1) multi[atomicAdd(nmulti, 1u)] = (uint16_t)(v + 1);
         cnt[w] = base | ((base + lo) << 16);
         base += lo + hi;
       }
@@ -548,16 +595,17 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
       opos[(old >> sh) & 0xffffu] = (uint16_t)e;
     }
     __syncthreads();
-    // 4. order inside each bucket: ascending position
-    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
+    // 4. order inside each bucket of two or more edges: ascending position
+    const uint32_t nm = *nmulti;
+    for (uint32_t i = threadIdx.x; i < nm; i += blockDim.x) {
+      const uint32_t v = multi[i];
       const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
       const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
       const uint32_t c = end - beg;
-      if (c < 2) continue;
       if (c <= kBinSmallBucket) {
-        for (uint32_t i = beg + 1; i < end; ++i) {
-          const uint16_t p = opos[i];
-          uint32_t j = i;
+        for (uint32_t k = beg + 1; k < end; ++k) {
+          const uint16_t p = opos[k];
+          uint32_t j = k;
           while (j > beg && opos[j - 1] > p) {
             opos[j] = opos[j - 1];
             --j;
@@ -614,19 +662,15 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
   }
 }
 
-// Bins too large for shared memory (duplicates, skew, tiny V): one CTA per
-// bin.  Pass 1 counts local buckets into shared-memory cursors and writes the
-// bin's offsets; pass 2 streams the bin in tiles, sorts each tile stably by
-// local bucket and appends every run at its bucket cursor.
-template <typename K, typename Map>
-__global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, const uint32_t* ovf_list,
-                                                               const uint32_t* ovf_count, Map map) {
-  constexpr int NW = kBinNW, IPT = kBigTile / (NW * 32);
-  extern __shared__ __align__(16) uint8_t smem[];
-  map.init();
-  const uint32_t nbmax = 1u << a.s;
-  uint8_t* sp = smem;
-  uint32_t* cur = (uint32_t*)sp; sp += align_up((size_t)nbmax * 4, 16);
+// Streams edges [start, start + len) of a bin in tiles of kBigTile, sorts
+// every tile stably by local bucket and appends each run at its bucket's
+// cursor (cur: absolute CSR positions of the bin's nb buckets, advanced).
+// Tiles follow input order and each is sorted stably, so every bucket keeps
+// ascending input position.
+template <typename K, typename Map, int NW>
+__device__ __forceinline__ void stream_runs(const BinArgs<K>& a, const Map& map, uint32_t start, uint32_t len,
+                                            uint64_t bucket0, uint32_t nb, uint32_t* cur, uint8_t* sp) {
+  constexpr int IPT = kBigTile / (NW * 32);
   K* tk = (K*)sp; sp += (size_t)kBigTile * sizeof(K);
   uint32_t* ti = (uint32_t*)sp; sp += (size_t)kBigTile * 4;
   uint16_t* lb = (uint16_t*)sp; sp += kBigTile * 2;
@@ -636,62 +680,173 @@ __global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, c
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wc = (uint32_t*)sp; sp += rank_words<NW>() * 4;
   uint32_t* wsum = (uint32_t*)sp;
+  for (uint32_t t0 = 0; t0 < len; t0 += kBigTile) {
+    const uint32_t cnt = min((uint32_t)kBigTile, len - t0);
+    for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const K key = a.in_k[start + t0 + e];
+      const uint32_t id = a.in_i[start + t0 + e];
+      tk[e] = key;
+      ti[e] = id;
+      lb[e] = (uint16_t)(map(key, id) - (uint32_t)bucket0);
+    }
+    __syncthreads();
+    const uint16_t* sorted = sort_positions_by_bucket<IPT, NW>(lb, cnt, nb, tmp, perm, wc, wsum);
+    for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) slb[j] = lb[sorted[j]];
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const uint16_t l = slb[j];
+      uint32_t lo = 0, hi = j;  // first index with slb == l
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (slb[mid] < l) lo = mid + 1; else hi = mid;
+      }
+      const uint32_t g = cur[l] + (j - lo);
+      const uint32_t p = sorted[j];
+      a.csr_k[g] = tk[p];
+      a.csr_i[g] = map.out_id(ti[p]);
+    }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const uint16_t l = slb[j];
+      if (j + 1 == cnt || slb[j + 1] != l) {
+        uint32_t lo = 0, hi = j;
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (slb[mid] < l) lo = mid + 1; else hi = mid;
+        }
+        cur[l] += j - lo + 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Local-bucket counts of edges [start, start + len) of a bin into cur[]
+// (zeroed first).  Equal buckets of a warp are merged by __match_any_sync,
+// so a bucket holding most of the bin (duplicates) costs one shared-memory
+// atomic per warp instead of one per edge.
+template <typename K, typename Map>
+__device__ __forceinline__ void count_local(const BinArgs<K>& a, const Map& map, uint32_t start, uint32_t len,
+                                            uint64_t bucket0, uint32_t nb, uint32_t* cur) {
+  for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) cur[v] = 0;
+  __syncthreads();
+  const uint32_t lane = lane_id();
+  for (uint32_t base = threadIdx.x & ~31u; base < len; base += blockDim.x) {
+    const uint32_t e = base + lane;
+    const bool valid = e < len;
+    const uint32_t l = valid ? map(a.in_k[start + e], a.in_i[start + e]) - (uint32_t)bucket0 : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(kFull, l);
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cur[l], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+}
+
+// Bins too large for shared memory (duplicates, skew, tiny V) with at most
+// kHugeSeg edges: one CTA per bin counts its local buckets, writes the bin's
+// offsets and streams the bin (stream_runs).
+template <typename K, typename Map>
+__global__ void __launch_bounds__(kBinNW * 32, 1) k_binbuild_big(BinArgs<K> a, const uint32_t* ovf_list,
+                                                               const uint32_t* ovf_count, Map map) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  map.init();
+  const uint32_t nbmax = 1u << a.s;
+  uint32_t* cur = (uint32_t*)smem;
+  uint8_t* rest = smem + align_up((size_t)nbmax * 4, 16);
+  uint32_t* wsum = (uint32_t*)(rest + big_rest_bytes(sizeof(K)) - 32 * 4);
   const uint32_t novf = *ovf_count;
   for (uint32_t k = blockIdx.x; k < novf; k += gridDim.x) {
     const uint32_t b = ovf_list[k];
     const uint32_t E = a.T[b], start = a.BS[b];
     const uint64_t bucket0 = (uint64_t)b << a.s;
     const uint32_t nb = (uint32_t)min((uint64_t)nbmax, a.V - bucket0);
-    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) cur[v] = 0;
-    __syncthreads();
-    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
-      atomicAdd(&cur[map(a.in_k[start + e], a.in_i[start + e]) - (uint32_t)bucket0], 1u);
-    __syncthreads();
+    count_local(a, map, start, E, bucket0, nb, cur);
     block_excl_scan_smem(cur, (int)nb, wsum);
     for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
       a.offsets[bucket0 + v] = a.pos_base + start + cur[v];
       cur[v] += start;
     }
     __syncthreads();
-    for (uint32_t t0 = 0; t0 < E; t0 += kBigTile) {
-      const uint32_t cnt = min((uint32_t)kBigTile, E - t0);
-      for (uint32_t e = threadIdx.x; e < cnt; e += blockDim.x) {
-        const K key = a.in_k[start + t0 + e];
-        const uint32_t id = a.in_i[start + t0 + e];
-        tk[e] = key;
-        ti[e] = id;
-        lb[e] = (uint16_t)(map(key, id) - (uint32_t)bucket0);
+    stream_runs<K, Map, kBinNW>(a, map, start, E, bucket0, nb, cur, rest);
+  }
+}
+
+// Bins above kHugeSeg edges, split into segments of kHugeSeg edges (rows).
+// 1. every row's local-bucket counts, one CTA per row
+template <typename K, typename Map>
+__global__ void __launch_bounds__(kBinNW * 32, 1) k_huge_count(BinArgs<K> a, const uint32_t* __restrict__ rows,
+                                                             const uint32_t* __restrict__ rowdesc,
+                                                             uint32_t* __restrict__ rowcnt, Map map) {
+  extern __shared__ __align__(16) uint32_t hcur[];
+  map.init();
+  const uint32_t nbmax = 1u << a.s;
+  const uint32_t R = *rows;
+  for (uint32_t r = blockIdx.x; r < R; r += gridDim.x) {
+    const uint32_t b = rowdesc[2 * r], sg = rowdesc[2 * r + 1];
+    const uint32_t off = sg * kHugeSeg;
+    const uint32_t len = min(kHugeSeg, a.T[b] - off);
+    const uint64_t bucket0 = (uint64_t)b << a.s;
+    const uint32_t nb = (uint32_t)min((uint64_t)nbmax, a.V - bucket0);
+    count_local(a, map, a.BS[b] + off, len, bucket0, nb, hcur);
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) rowcnt[(uint64_t)r * nbmax + v] = hcur[v];
+    __syncthreads();
+  }
+}
+
+// 2. per huge bin: bucket totals over its rows, exclusive scan -> the bin's
+//    offsets; every row's counts become its absolute CSR cursors
+template <typename K>
+__global__ void __launch_bounds__(1024) k_huge_scan(BinArgs<K> a, const uint32_t* __restrict__ hcount,
+                                                    const uint32_t* __restrict__ hlist, uint32_t* __restrict__ rowcnt) {
+  extern __shared__ __align__(16) uint32_t tot[];
+  __shared__ uint32_t wsum[32];
+  const uint32_t nbmax = 1u << a.s;
+  const uint32_t H = *hcount;
+  for (uint32_t k = blockIdx.x; k < H; k += gridDim.x) {
+    const uint32_t b = hlist[3 * k], r0 = hlist[3 * k + 1], nr = hlist[3 * k + 2];
+    const uint64_t bucket0 = (uint64_t)b << a.s;
+    const uint32_t nb = (uint32_t)min((uint64_t)nbmax, a.V - bucket0);
+    const uint32_t start = a.BS[b];
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
+      uint32_t run = 0;
+      for (uint32_t r = 0; r < nr; ++r) {
+        uint32_t* p = rowcnt + (uint64_t)(r0 + r) * nbmax + v;
+        const uint32_t c = *p;
+        *p = run;
+        run += c;
       }
-      __syncthreads();
-      const uint16_t* sorted = sort_positions_by_bucket<IPT, NW>(lb, cnt, nb, tmp, perm, wc, wsum);
-      for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) slb[j] = lb[sorted[j]];
-      __syncthreads();
-      for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
-        const uint16_t l = slb[j];
-        uint32_t lo = 0, hi = j;  // first index with slb == l
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (slb[mid] < l) lo = mid + 1; else hi = mid;
-        }
-        const uint32_t g = cur[l] + (j - lo);
-        const uint32_t p = sorted[j];
-        a.csr_k[g] = tk[p];
-        a.csr_i[g] = map.out_id(ti[p]);
-      }
-      __syncthreads();
-      for (uint32_t j = threadIdx.x; j < cnt; j += blockDim.x) {
-        const uint16_t l = slb[j];
-        if (j + 1 == cnt || slb[j + 1] != l) {
-          uint32_t lo = 0, hi = j;
-          while (lo < hi) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (slb[mid] < l) lo = mid + 1; else hi = mid;
-          }
-          cur[l] += j - lo + 1;
-        }
-      }
-      __syncthreads();
+      tot[v] = run;
     }
+    __syncthreads();
+    block_excl_scan_smem(tot, (int)nb, wsum);
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
+      const uint32_t first = start + tot[v];
+      a.offsets[bucket0 + v] = a.pos_base + first;
+      for (uint32_t r = 0; r < nr; ++r) rowcnt[(uint64_t)(r0 + r) * nbmax + v] += first;
+    }
+    __syncthreads();
+  }
+}
+
+// 3. every row streams its segment to its cursors, one CTA per row
+template <typename K, typename Map>
+__global__ void __launch_bounds__(kBinNW * 32, 1) k_huge_scatter(BinArgs<K> a, const uint32_t* __restrict__ rows,
+                                                               const uint32_t* __restrict__ rowdesc,
+                                                               const uint32_t* __restrict__ rowcnt, Map map) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  map.init();
+  const uint32_t nbmax = 1u << a.s;
+  uint32_t* cur = (uint32_t*)smem;
+  uint8_t* rest = smem + align_up((size_t)nbmax * 4, 16);
+  const uint32_t R = *rows;
+  for (uint32_t r = blockIdx.x; r < R; r += gridDim.x) {
+    const uint32_t b = rowdesc[2 * r], sg = rowdesc[2 * r + 1];
+    const uint32_t off = sg * kHugeSeg;
+    const uint32_t len = min(kHugeSeg, a.T[b] - off);
+    const uint64_t bucket0 = (uint64_t)b << a.s;
+    const uint32_t nb = (uint32_t)min((uint64_t)nbmax, a.V - bucket0);
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) cur[v] = rowcnt[(uint64_t)r * nbmax + v];
+    __syncthreads();
+    stream_runs<K, Map, kBinNW>(a, map, a.BS[b] + off, len, bucket0, nb, cur, rest);
   }
 }
 
@@ -867,8 +1022,15 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   const bool two = p.sshift > 0;
   {
     HG_TRACE("k_scan_bins", st);
+    HugeArgs h{};
+    h.list = (uint32_t*)(ws + p.o_hlist);
+    h.count = (uint32_t*)&hdr->counters[0];
+    h.rows = (uint32_t*)&hdr->counters[0] + 1;
+    h.rowdesc = (uint32_t*)(ws + p.o_rowdesc);
+    h.max_rows = p.max_rows;
+    h.status = status;
     k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, p.emax, ovf, &hdr->ovf_count, offsets, p.V,
-                                    pos_base + (uint32_t)p.n);
+                                    pos_base + (uint32_t)p.n, h);
   }
 
   PartArgs<K> pa{};
@@ -966,6 +1128,28 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
       HG_TRACE("k_binbuild_big", st);
       kern<<<grid, kBinNW * 32, sm, st>>>(ba, ovf, &hdr->ovf_count, map);
     }
+  }
+  if (p.n > kHugeSeg) {
+    // bins above kHugeSeg edges (duplicates): several CTAs per bin
+    const uint32_t nbmax = 1u << p.s;
+    uint32_t* hcount = (uint32_t*)&hdr->counters[0];
+    uint32_t* hrows = hcount + 1;
+    const uint32_t* hlist = (const uint32_t*)(ws + p.o_hlist);
+    const uint32_t* rowdesc = (const uint32_t*)(ws + p.o_rowdesc);
+    uint32_t* rowcnt = (uint32_t*)(ws + p.o_rowcnt);
+    const unsigned grid = (unsigned)std::min<uint64_t>(p.max_rows, (uint64_t)di.sms);
+    const unsigned hgrid = (unsigned)std::min<uint64_t>(p.n / kHugeSeg + 1, (uint64_t)di.sms);
+    HG_TRACE("k_binbuild_huge", st);
+    auto kc = k_huge_count<K, Map>;
+    set_smem_once(kc, (size_t)nbmax * 4);
+    kc<<<grid, kBinNW * 32, (size_t)nbmax * 4, st>>>(ba, hrows, rowdesc, rowcnt, map);
+    auto ks = k_huge_scan<K>;
+    set_smem_once(ks, (size_t)nbmax * 4);
+    ks<<<hgrid, 1024, (size_t)nbmax * 4, st>>>(ba, hcount, hlist, rowcnt);
+    const size_t sm = big_smem_bytes(sizeof(K), nbmax);
+    auto kx = k_huge_scatter<K, Map>;
+    set_smem_once(kx, sm);
+    kx<<<grid, kBinNW * 32, sm, st>>>(ba, hrows, rowdesc, rowcnt, map);
   }
   return last_launch_status();
 }
@@ -1179,7 +1363,7 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
     HG_TRACE("k_scan_Q", st);
     // no bin is "oversized" here; the closing-offset store goes to scratch
     k_scan_bins<<<1, 1024, 0, st>>>(CT, p.ng, GS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.ng, 0,
-                                    (uint32_t)q);
+                                    (uint32_t)q, HugeArgs{});
   }
   PartArgs<K> pa{};
   pa.in_k = queries;
@@ -1293,7 +1477,8 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
     {
       HG_TRACE("k_radix_scan", st);
       k_colscan<<<1, 256, 0, st>>>(C, G, 256, CT);
-      k_scan_bins<<<1, 1024, 0, st>>>(CT, 256, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + 256, 0, (uint32_t)n);
+      k_scan_bins<<<1, 1024, 0, st>>>(CT, 256, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + 256, 0, (uint32_t)n,
+                                      HugeArgs{});
     }
     PartArgs<uint64_t> pa{};
     pa.in_k = src;

@@ -41,9 +41,10 @@ constexpr int kPartTile = kPartNW * 32 * kPartIPT;  // 4096 elements per tile
 #endif
 constexpr int kBinNW = HG_BIN_NW;      // warps of the bin-build kernels (1024 threads)
 constexpr int kBigTile = 2048;         // tile of the oversized-bin kernel
-constexpr uint32_t kBinEmaxU32 = 10240; // largest bin built in shared memory (uint32 keys)
+constexpr uint32_t kBinEmaxU32 = 9216;  // largest bin built in shared memory (uint32 keys)
 constexpr uint32_t kBinEmaxU64 = 7168;  // same for uint64 keys
 constexpr uint32_t kBinSmallBucket = 32; // bucket length sorted by one thread in the bin build
+constexpr uint32_t kHugeSeg = 1u << 17;  // bins above this many edges are built by several CTAs, one per segment
 constexpr uint32_t kBinBitmapWarps = 16; // warps sorting longer buckets with position bitmaps
 constexpr uint32_t kV1Small = 32;      // V1 fix-up: longest bucket sorted by one thread
 constexpr int kV1HeavyNW = 16;
@@ -59,7 +60,8 @@ struct Plan {
   uint64_t chunk;    // elements per chunk (multiple of 16)
   uint32_t emax;     // largest bin built in shared memory
   uint32_t tpb;      // threads per bin-build CTA (512 or 1024)
-  size_t o_H, o_C, o_CT, o_T, o_BS, o_ovf, o_bk, o_bi, total;
+  uint32_t max_rows; // segments of huge bins (bins above kHugeSeg edges), upper bound
+  size_t o_H, o_C, o_CT, o_T, o_BS, o_ovf, o_hlist, o_rowdesc, o_rowcnt, o_bk, o_bi, total;
 };
 
 bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p);

@@ -60,6 +60,31 @@ def test_build_all_keys_equal_and_single_bucket(hg, orc):
         _check_build(hg, orc, dg.uniform_keys_u32(70_000, 8), 1, algo=algo)
 
 
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+def test_build_huge_bins_split_across_ctas(hg, orc, kt):
+    # Two keys hold 40% and 20% of 2^21 keys: their bins exceed 2^17 edges and
+    # are built by several CTAs, one per 2^17-edge segment; the rest of the
+    # table stays on the shared-memory path.
+    n = 1 << 21
+    base = dg.uniform_keys_u32(n, 21) if kt == "u32" else dg.uniform_keys_u64(n, 21)
+    sel = dg.splitmix64(21, 99, np.arange(n, dtype=np.uint64)) >> np.uint64(11)
+    u = sel.astype(np.float64) / float(1 << 53)
+    keys = base.copy()
+    keys[u < 0.4] = base[0]
+    keys[(u >= 0.4) & (u < 0.6)] = base[1]
+    for algo in ("v2", "v1"):
+        _check_build(hg, orc, keys, 1 << 20, algo=algo)
+
+
+@pytest.mark.parametrize("n", [3 << 17, (3 << 17) + 1, 1 << 20])
+def test_build_single_bucket_segment_edges(hg, orc, n):
+    # one bin, one bucket: exactly k segments, k segments plus one edge, and
+    # 2^20 equal keys
+    keys = dg.uniform_keys_u32(n, 5)
+    _check_build(hg, orc, keys, 1, algo="v2")
+    _check_build(hg, orc, np.full(n, 77, dtype=np.uint32), 1 << 12, algo="v2")
+
+
 def test_build_zipf_u64(hg, orc):
     keys = dg.zipf_keys_u64(1 << 20, 1 << 16, 7)
     for algo in ("v2", "v1"):
