@@ -86,6 +86,30 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_bucket(const uint32_t* __
   }
 }
 
+// Pairs of a warp's 32 consecutive A edges occupy one contiguous output
+// range; it is written in windows of kJoinWin pairs: every lane stages the
+// pairs of its edge that fall in the window in shared memory, then the warp
+// writes the window out coalesced.
+constexpr uint32_t kJoinWin = 256;
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t x) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const uint64_t y = __shfl_xor_sync(kFull, x, d);
+    x = y < x ? y : x;
+  }
+  return x;
+}
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t x) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const uint64_t y = __shfl_xor_sync(kFull, x, d);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
 template <typename K, typename Map>
 __global__ void __launch_bounds__(kJoinThreads) k_join_write(const K* __restrict__ keysA,
                                                              const uint32_t* __restrict__ idsA, uint64_t nA,
@@ -96,20 +120,49 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(const K* __restrict
                                                              int64_t* __restrict__ outA,
                                                              int64_t* __restrict__ outB, uint64_t cap,
                                                              Map map) {
+  __shared__ int64_t stage_a[kJoinThreads / 32][kJoinWin];
+  __shared__ int64_t stage_b[kJoinThreads / 32][kJoinWin];
   map.init();
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nA; j += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t o = moff[j];
-    if (o >= cap || moff[j + 1] == o) continue;
-    const K key = keysA[j];
-    const uint32_t v = map(key);
-    const int64_t ida = idsA[j];
-    const uint32_t s = __ldg(offB + v), e = __ldg(offB + v + 1);
-    for (uint32_t k = s; k < e && o < cap; ++k)
-      if (__ldg(keysB + k) == key) {
-        outA[o] = ida;
-        outB[o] = __ldg(idsB + k);
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  int64_t* sa = stage_a[w];
+  int64_t* sb = stage_b[w];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nA; base += stride) {
+    const uint64_t j = base + lane;
+    const bool valid = j < nA;
+    uint64_t o = valid ? moff[j] : ~0ull, oe = valid ? moff[j + 1] : 0ull;
+    if (oe > cap) oe = cap;
+    K key = K(0);
+    int64_t ida = 0;
+    uint32_t k = 0, e = 0;
+    if (valid && o < oe) {
+      key = keysA[j];
+      ida = idsA[j];
+      const uint32_t v = map(key);
+      k = __ldg(offB + v);
+      e = __ldg(offB + v + 1);
+    }
+    const uint64_t lo = warp_min_u64(o), hi = warp_max_u64(oe);
+    for (uint64_t w0 = lo; w0 < hi; w0 += kJoinWin) {
+      const uint64_t w1 = w0 + kJoinWin < hi ? w0 + kJoinWin : hi;
+      while (o < oe && o < w1) {
+        while (k < e && __ldg(keysB + k) != key) ++k;
+        if (k >= e) {  // unreachable for the tables the counts came from; keeps k inside the bucket
+          oe = o;
+          break;
+        }
+        sa[o - w0] = ida;
+        sb[o - w0] = __ldg(idsB + k);
         ++o;
+        ++k;
       }
+      __syncwarp();
+      for (uint64_t i = w0 + lane; i < w1; i += 32) {
+        outA[i] = sa[i - w0];
+        outB[i] = sb[i - w0];
+      }
+      __syncwarp();
+    }
   }
 }
 

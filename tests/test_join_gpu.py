@@ -71,3 +71,25 @@ def test_join_empty_sides(hg):
     assert int(hg.join_count(tB, tA)[0].item()) == 0
     pa, pb = hg.join_materialize(tB, tA)
     assert pa.numel() == 0
+
+
+@pytest.mark.parametrize("V", [1, 1 << 10])
+def test_join_materialize_long_pair_lists(hg, orc, V):
+    # 3000 copies of one key against 1500 copies of it: every such A edge
+    # writes 1500 pairs, spanning many output windows; the other keys share
+    # the bucket with it when V = 1; a capacity cut inside a window
+    u = dg.uniform_keys_u32(8000, 41)
+    a = np.concatenate([np.full(3000, u[0], dtype=np.uint32), u[1:5001]])
+    b = np.concatenate([np.full(1500, u[0], dtype=np.uint32), u[2000:5000]])
+    pa_ = dg.splitmix64(3, 7, np.arange(len(a), dtype=np.uint64)).argsort(kind="stable")
+    pb_ = dg.splitmix64(3, 8, np.arange(len(b), dtype=np.uint64)).argsort(kind="stable")
+    a, b = a[pa_], b[pb_]
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V, seed=6)
+    pa, pb = hg.join_materialize(tA, tB)
+    ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V)
+    assert len(ra) == 3000 * 1500 + 3000
+    assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
+    cap = 1_234_567
+    pa, pb = hg.join_materialize(tA, tB, capacity=cap)
+    ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V, cap=cap)
+    assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
