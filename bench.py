@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--log2n", type=int, default=None)
     ap.add_argument("--log2v", type=int, default=None)
     ap.add_argument("--hit", type=float, default=0.5)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--standard-probe", action="store_true", help="time HashGraph-Probe-Standard instead of the binned probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
@@ -403,20 +403,54 @@ def run_scale(c: Ctx):
 
     e2e = None
     if args.e2e_steps > 0:
-        counts_h = torch.empty(q, dtype=torch.int32).pin_memory()
-        kd2 = torch.empty(n, dtype=torch.int32, device=c.dev)
-        qd2 = torch.empty(q, dtype=torch.int32, device=c.dev)
+        # Through the public host-buffer call (hg_build_probe_host): keys and
+        # queries from pinned host memory, counts back to pinned host memory,
+        # every step.  Two batches in flight on two streams, as a serving loop
+        # would run it, so one batch's copies overlap the other's kernels.
+        del ws, offsets, ck, ci, counts, pws, table
+        slots = []
+        for _ in range(2):
+            sl = {"stream": torch.cuda.Stream(device=c.dev),
+                  "dk": torch.empty(n, dtype=torch.uint32, device=c.dev),
+                  "dq": torch.empty(q, dtype=torch.uint32, device=c.dev),
+                  "dc": torch.empty(q, dtype=torch.uint32, device=c.dev),
+                  "table": hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=c.dev),
+                                    torch.empty(n, dtype=torch.uint32, device=c.dev),
+                                    torch.empty(n, dtype=torch.uint32, device=c.dev), cfg),
+                  "hc": torch.empty(q, dtype=torch.int32).pin_memory()}
+            sl["ws"] = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=c.dev)
+            sl["pws"] = (torch.empty(hg.probe_workspace_size(sl["table"], q), dtype=torch.uint8, device=c.dev)
+                         if binned else None)
+            slots.append(sl)
 
-        def e2e_step():
-            kd2.copy_(keys_p, non_blocking=True)
-            qd2.copy_(q_p, non_blocking=True)
-            step(kd2.view(torch.uint32), qd2.view(torch.uint32))
-            counts_h.copy_(counts.view(torch.int32), non_blocking=True)
+        def host_step(i):
+            sl = slots[i % 2]
+            hg.build_probe_host(cfg, keys_p, q_p, sl["hc"], sl["dk"], sl["dq"], sl["dc"], sl["table"], sl["ws"],
+                                sl["pws"], stream=sl["stream"])
 
-        e2e_ms, _, _ = c.timed(e2e_step, args.e2e_steps, profile=False)
+        for i in range(2):   # warm-up of both slots
+            host_step(i)
+        torch.cuda.synchronize()
+        c.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        for sl in slots:
+            sl["stream"].wait_stream(c.stream)
+        for i in range(args.e2e_steps):
+            host_step(i)
+        for sl in slots:
+            c.stream.wait_stream(sl["stream"])
+        e1.record(c.stream)
+        torch.cuda.synchronize()
+        c.barrier()
+        e2e_ms = c.max_over_ranks(e0.elapsed_time(e1))
+        ok = bool(np.array_equal(slots[(args.e2e_steps - 1) % 2]["hc"].numpy().view(np.uint32),
+                                 slots[(args.e2e_steps - 1) % 2]["dc"].cpu().numpy()))
         e2e = {"value": c.world * (n + q) * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": 4 * (n + q), "d2h_bytes_per_step": 4 * q}
-        del kd2, qd2
+               "h2d_bytes_per_step": 4 * (n + q), "d2h_bytes_per_step": 4 * q,
+               "call": "hg_build_probe_host, pinned host buffers, 2 batches in flight", "counts_returned": ok}
+        del slots
 
     cpu = None
     if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:

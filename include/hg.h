@@ -119,6 +119,22 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
                           uint64_t q, uint32_t* d_counts, void* d_ws, size_t ws_bytes,
                           void* stream);
 
+/* -------------------------------------------------------- host buffers --
+ * Build and probe with inputs and results in host memory, one call: keys
+ * and queries are copied host -> device into the caller's staging buffers
+ * (d_keys [n], d_queries [q]), the table is built into `table` (device
+ * buffers of n keys, table->n must equal n) with implicit ids, the queries
+ * are probed (binned when d_probe_ws is given, else direct) into d_counts
+ * [q], and the counts are copied back to h_counts [q].  Everything is
+ * asynchronous on `stream` (host buffers should be pinned for the copies to
+ * overlap other work); h_counts is valid after the stream is synchronised.
+ * Workspaces as for hg_build and hg_probe_binned.  No counterpart in the
+ * paper: it is the whole hot path behind one call. */
+hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t n, const void* h_queries,
+                              uint64_t q, uint32_t* h_counts, void* d_keys, void* d_queries, uint32_t* d_counts,
+                              const hg_table* table, void* d_build_ws, size_t build_ws_bytes, void* d_probe_ws,
+                              size_t probe_ws_bytes, void* stream);
+
 /* ----------------------------------------------------------------- join --
  * HashGraph-Probe-New (Alg. 3, Section 3.4): both inputs are built into
  * tables with the same V and map; bucket v of A is intersected with bucket v

@@ -80,6 +80,7 @@ SIGNATURES = {
     "hg_batch_run_eager": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_static_scratch_bytes": (_SZ, []),
     "hg_build_static_scratch": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
+    "hg_build_probe_host": (_I32, [_CFGP, _VP, _U64, _VP, _U64, _VP, _VP, _VP, _VP, _TABP, _VP, _SZ, _VP, _SZ, _VP]),
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
     "hg_join_count": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_join_materialize": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
@@ -287,6 +288,21 @@ def probe(table: Table, queries, stream=None, binned: bool | None = None, ws=Non
     else:
         probe_into(table, queries, counts, stream)
     return counts
+
+
+def build_probe_host(cfg: hg_config, h_keys, h_queries, h_counts, d_keys, d_queries, d_counts, table: Table,
+                     ws, probe_ws=None, stream=None):
+    """hg_build_probe_host: host keys/queries in, host counts out (pinned CPU
+    tensors), device staging and table buffers given; asynchronous."""
+    for name, t in (("h_keys", h_keys), ("h_queries", h_queries), ("h_counts", h_counts)):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    tv = table.view()
+    _check(load().hg_build_probe_host(ctypes.byref(cfg), _ptr(h_keys), h_keys.numel(), _ptr(h_queries),
+                                      h_queries.numel(), _ptr(h_counts), _ptr(d_keys), _ptr(d_queries),
+                                      _ptr(d_counts), ctypes.byref(tv), _ptr(ws), ws.numel(), _ptr(probe_ws),
+                                      0 if probe_ws is None else probe_ws.numel(), _stream_handle(stream)),
+           "hg_build_probe_host")
 
 
 def join_workspace_size(cfg: hg_config, nA: int, nB: int) -> int:

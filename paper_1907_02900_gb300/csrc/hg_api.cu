@@ -171,6 +171,31 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
   });
 }
 
+hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t n, const void* h_queries,
+                              uint64_t q, uint32_t* h_counts, void* d_keys, void* d_queries, uint32_t* d_counts,
+                              const hg_table* table, void* d_build_ws, size_t build_ws_bytes, void* d_probe_ws,
+                              size_t probe_ws_bytes, void* stream) {
+  hg_status rc = validate_config(cfg);
+  if (rc != HG_OK) return rc;
+  if (!table || table->n != n || (n > 0 && (!h_keys || !d_keys)) || (q > 0 && (!h_queries || !h_counts)))
+    return HG_ERR_INVALID_ARG;
+  const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n > 0 && cudaMemcpyAsync(d_keys, h_keys, n * kb, cudaMemcpyHostToDevice, st) != cudaSuccess) return HG_ERR_CUDA;
+  if (q > 0 && cudaMemcpyAsync(d_queries, h_queries, q * kb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HG_ERR_CUDA;
+  // the table's buffers are this call's output (hg_table carries them as const for probes)
+  rc = hg_build(cfg, d_keys, nullptr, n, const_cast<uint32_t*>(table->d_offsets), const_cast<void*>(table->d_keys),
+                const_cast<uint32_t*>(table->d_ids), d_build_ws, build_ws_bytes, stream);
+  if (rc != HG_OK) return rc;
+  if (q == 0) return HG_OK;
+  rc = d_probe_ws ? hg_probe_binned(cfg, table, d_queries, q, d_counts, d_probe_ws, probe_ws_bytes, stream)
+                  : hg_probe(cfg, table, d_queries, q, d_counts, stream);
+  if (rc != HG_OK) return rc;
+  if (cudaMemcpyAsync(h_counts, d_counts, q * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HG_ERR_CUDA;
+  return HG_OK;
+}
+
 size_t hg_join_workspace_size(const hg_config* cfg, uint64_t nA, uint64_t nB) {
   (void)nB;
   if (validate_config(cfg) != HG_OK) return 0;

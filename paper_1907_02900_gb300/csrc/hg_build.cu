@@ -1231,8 +1231,11 @@ __global__ void k_scatter_counts(const uint32_t* __restrict__ Qi, const uint32_t
     counts[__ldcs(Qi + j)] = __ldcs(Qc + j);
 }
 
+#ifndef HG_UNPERMUTE_TILE
+#define HG_UNPERMUTE_TILE 32768
+#endif
 constexpr int kUnpermuteThreads = 1024;
-constexpr uint32_t kUnpermuteTile = 8192;
+constexpr uint32_t kUnpermuteTile = HG_UNPERMUTE_TILE;  // outputs per merge tile (shared memory: 4 B each)
 constexpr int kUnpermuteGPW = 8;  // groups per warp: 256 groups / 32 warps
 
 __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t* __restrict__ Qi,
@@ -1241,7 +1244,7 @@ __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t*
                                                                  uint64_t Q, uint64_t span,
                                                                  uint32_t* __restrict__ counts) {
   __shared__ uint32_t cur[256], gend[256];
-  __shared__ uint32_t out_s[kUnpermuteTile];
+  extern __shared__ uint32_t out_s[];  // kUnpermuteTile entries
   const uint64_t ob = (uint64_t)blockIdx.x * span;
   if (ob >= Q) return;
   const uint64_t oe = min(ob + span, Q);
@@ -1400,8 +1403,11 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
     if (Map::kNeedsPos)
       k_scatter_counts<<<(unsigned)std::min<uint64_t>((q + 255) / 256, (uint64_t)di.sms * 16), 256, 0, st>>>(
           qi, qc, q, counts);
-    else
-      k_unpermute<<<(unsigned)grid, kUnpermuteThreads, 0, st>>>(qi, qc, GS, p.ng, q, span, counts);
+    else {
+      set_smem_once(k_unpermute, (size_t)kUnpermuteTile * 4);
+      k_unpermute<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.ng, q, span,
+                                                                                         counts);
+    }
   }
   return last_launch_status();
 }

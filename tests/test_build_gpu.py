@@ -186,3 +186,32 @@ def test_full_size_build_and_probe_sampled(hg, orc):
     assert np.array_equal(counts[qi], want)
     del t, dk
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("binned", [True, False])
+def test_build_probe_host_buffers(hg, orc, pinned, binned):
+    import torch
+    n, V = (1 << 18) + 3, 1 << 18
+    keys = dg.uniform_keys_u32(n, 61)
+    q = dg.queries_u32(n + 11, keys, 0.5, 62)
+    hk = torch.from_numpy(keys.view(np.int32).copy())
+    hq = torch.from_numpy(q.view(np.int32).copy())
+    hc = torch.zeros(len(q), dtype=torch.int32)
+    if pinned:
+        hk, hq, hc = hk.pin_memory(), hq.pin_memory(), hc.pin_memory()
+    cfg = hg.make_config(hg.KEY_U32, V, 0, "v2")
+    dev = "cuda"
+    t = hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=dev), torch.empty(n, dtype=torch.uint32, device=dev),
+                 torch.empty(n, dtype=torch.uint32, device=dev), cfg)
+    ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=dev)
+    pws = torch.empty(hg.probe_workspace_size(t, len(q)), dtype=torch.uint8, device=dev) if binned else None
+    dk = torch.empty(n, dtype=torch.uint32, device=dev)
+    dq = torch.empty(len(q), dtype=torch.uint32, device=dev)
+    dc = torch.empty(len(q), dtype=torch.uint32, device=dev)
+    hg.build_probe_host(cfg, hk, hq, hc, dk, dq, dc, t, ws, pws)
+    torch.cuda.synchronize()
+    assert np.array_equal(hc.numpy().view(np.uint32), orc.multiplicity(keys, q))
+    off, ck, ci = table_np(t)
+    roff, rk, ri = orc.build(keys, V)
+    assert np.array_equal(off, roff) and np.array_equal(ck, rk) and np.array_equal(ci, ri)
