@@ -254,6 +254,12 @@ class Ctx:
         if self.world > 1:
             self.torch.distributed.barrier()
 
+    def rate(self, units_local: float, elapsed_ms_local: float) -> tuple[float, float]:
+        """(Gunits/s summed over ranks, slowest rank's ms)."""
+        from paper_1907_02900_gb300.replicas import whole_job_rate
+        r, ms = whole_job_rate(units_local, elapsed_ms_local, self.dev if self.world > 1 else None)
+        return r / 1e9, ms
+
     def max_over_ranks(self, x: float) -> float:
         if self.world == 1:
             return x
@@ -263,7 +269,7 @@ class Ctx:
 
     def timed(self, fn, steps: int, profile: bool = True):
         """Run fn() `steps` times between CUDA events (barrier + sync on both
-        sides); returns (max-over-ranks ms, clocks, per-kernel profile)."""
+        sides); returns (this rank's ms, clocks, per-kernel profile)."""
         torch, hg = self.torch, self.hg
         sampler = ClockSampler(self.local) if self.rank == 0 else None
         hg.profile_reset()
@@ -284,7 +290,7 @@ class Ctx:
         hg.profile_enable(False)
         prof = hg.profile_read() if profile else {}
         hg.profile_reset()
-        return self.max_over_ranks(e0.elapsed_time(e1)), clocks, prof
+        return e0.elapsed_time(e1), clocks, prof
 
     def line(self, workload: str, value: float, ms_per_step: float, dtype: str, config: dict, **extra) -> dict:
         a = self.args
@@ -392,9 +398,9 @@ def run_scale(c: Ctx):
     c.check_ws(ws, "build")
     if binned:
         c.check_ws(pws, "probe")
-    elapsed_ms, clocks, prof = c.timed(lambda: step(keys_d, q_d), args.steps)
+    local_ms, clocks, prof = c.timed(lambda: step(keys_d, q_d), args.steps)
+    value, elapsed_ms = c.rate((n + q) * args.steps, local_ms)
     ms_per_step = elapsed_ms / args.steps
-    value = c.world * (n + q) * args.steps / (elapsed_ms * 1e-3) / 1e9
     algo = dict(algo_build(4, n, V), **algo_probe(4, n, V, q, args.hit, binned))
     units = {k: (q if k in PROBE_KERNELS else n) for k in algo}
     roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
@@ -444,10 +450,10 @@ def run_scale(c: Ctx):
         e1.record(c.stream)
         torch.cuda.synchronize()
         c.barrier()
-        e2e_ms = c.max_over_ranks(e0.elapsed_time(e1))
+        e2e_value, _ = c.rate((n + q) * args.e2e_steps, e0.elapsed_time(e1))
         ok = bool(np.array_equal(slots[(args.e2e_steps - 1) % 2]["hc"].numpy().view(np.uint32),
                                  slots[(args.e2e_steps - 1) % 2]["dc"].cpu().numpy()))
-        e2e = {"value": c.world * (n + q) * args.e2e_steps / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * (n + q), "d2h_bytes_per_step": 4 * q,
                "call": "hg_build_probe_host, pinned host buffers, 2 batches in flight", "counts_returned": ok}
         del slots
@@ -517,9 +523,9 @@ def run_join(c: Ctx):
     torch.cuda.synchronize()
     c.check_ws(ws, "build")
     c.check_ws(jws, "join")
-    elapsed_ms, clocks, prof = c.timed(step, args.steps)
+    local_ms, clocks, prof = c.timed(step, args.steps)
+    value, elapsed_ms = c.rate(2 * n * args.steps, local_ms)
     ms = elapsed_ms / args.steps
-    value = c.world * 2 * n / (ms * 1e-3) / 1e9
     # two builds per step
     algo = {k: 2 * v for k, v in algo_build(8, n, V).items()}
     algo.update(algo_join(8, n, n, V, M))
@@ -544,7 +550,7 @@ def run_join(c: Ctx):
                           "the same values into 2^27 buckets each (V2), join count + materialise int64 pairs",
               "global_batch": c.world * 2 * n, "l2": "inputs exceed L2; no flush",
               "parallelism": f"replicas x{c.world}", "pairs": M}
-    return c.line("join", value, ms, "u64", config, pairs_per_s=round(c.world * M / (ms * 1e-3) / 1e9, 3),
+    return c.line("join", value, ms, "u64", config, pairs_per_s=round(c.rate(M * args.steps, local_ms)[0], 3),
                   join_ms=round(join_ms, 3), roofline=roof, phases=phases, cpu_baseline=cpu, e2e=None,
                   gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
 
@@ -568,9 +574,9 @@ def run_batched(c: Ctx):
     torch.cuda.synchronize()
     c.check_ws(b["ws"], "batch")
     units = int(sizes.sum() + qsizes.sum())
-    elapsed_ms, clocks, _ = c.timed(lambda: plan.run(b), args.steps, profile=False)
+    local_ms, clocks, _ = c.timed(lambda: plan.run(b), args.steps, profile=False)
+    value, elapsed_ms = c.rate(units * args.steps, local_ms)
     ms = elapsed_ms / args.steps
-    value = c.world * units / (ms * 1e-3) / 1e9
     # per-kernel breakdown from one eager (uncaptured) run of the same sequence
     eager_ms, _, prof = c.timed(lambda: plan.run_eager(b), 1)
     n, q, V = int(plan.total_keys), int(plan.total_queries), int(plan.total_offsets - 1)
@@ -588,7 +594,7 @@ def run_batched(c: Ctx):
         plan.run_plain(b)
         torch.cuda.synchronize()
         pm, _, _ = c.timed(lambda: plan.run_plain(b), args.plain_steps, profile=False)
-        plain_ms = pm / args.plain_steps
+        plain_ms = c.max_over_ranks(pm) / args.plain_steps
         plan.run(b)
     cpu = None
     if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:
@@ -614,7 +620,7 @@ def run_batched(c: Ctx):
               "parallelism": f"replicas x{c.world}", "autotuned": tuned, "autotune_s": round(tune_s, 2),
               "waves": plan.config()["waves"]}
     return c.line("batched", value, ms, "u32", config,
-                  plain_loop_gkeys_s=round(units / (plain_ms * 1e-3) / 1e9, 3) if plain_ms else None,
+                  plain_loop_gkeys_s=round(c.world * units / (plain_ms * 1e-3) / 1e9, 3) if plain_ms else None,
                   speedup_vs_plain_loop=round(plain_ms / ms, 2) if plain_ms else None,
                   roofline=roof, phases=phases, cpu_baseline=cpu, e2e=None,
                   gpu_launches=sum(v[1] for v in prof.values()) * args.steps, clocks=clocks)
@@ -670,9 +676,9 @@ def run_learned(c: Ctx):
         del ws, pws
     same_counts = bool(torch.equal(res["learned"][3], res["murmur"][3]))
     el, clocks, prof, _ = res["learned"]
-    ms = el / args.steps
-    value = c.world * (n + q) / (ms * 1e-3) / 1e9
-    murmur_value = c.world * (n + q) / (res["murmur"][0] / args.steps * 1e-3) / 1e9
+    value, el_max = c.rate((n + q) * args.steps, el)
+    ms = el_max / args.steps
+    murmur_value, _ = c.rate((n + q) * args.steps, res["murmur"][0])
     algo = dict(algo_build(8, n, V), **algo_probe(8, n, V, q, args.hit, True))
     units = {k: (q if k in PROBE_KERNELS else n) for k in algo}
     roof, phases = roofline(prof, algo, args.steps, el, c.hbm, c.peak_src, units)

@@ -135,6 +135,16 @@ hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t
                               const hg_table* table, void* d_build_ws, size_t build_ws_bytes, void* d_probe_ws,
                               size_t probe_ws_bytes, void* stream);
 
+/* ----------------------------------------------------------- self-test --
+ * Every wait inside the kernels (TMA copy completion on an mbarrier) is
+ * bounded: after 2 s it records HG_ERR_TIMEOUT in the workspace status and
+ * the kernel returns, so the context stays usable.  This call exercises that
+ * path on purpose: one CTA waits on a barrier that is never completed (it
+ * expects two arrivals and gets one) with a limit of limit_ms (1..5000); the
+ * workspace status (first 256 bytes of d_ws) then reads HG_ERR_TIMEOUT.  No
+ * counterpart in the paper. */
+hg_status hg_selftest_wait_timeout(void* d_ws, uint32_t limit_ms, void* stream);
+
 /* ----------------------------------------------------------------- join --
  * HashGraph-Probe-New (Alg. 3, Section 3.4): both inputs are built into
  * tables with the same V and map; bucket v of A is intersected with bucket v

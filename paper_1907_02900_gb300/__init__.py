@@ -84,6 +84,7 @@ SIGNATURES = {
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
     "hg_join_count": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_join_materialize": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
+    "hg_selftest_wait_timeout": (_I32, [_VP, _U32, _VP]),
     "hg_workspace_status": (_I32, [_VP, _VP]),
     "hg_workspace_clear": (_I32, [_VP, _VP]),
     "hg_profile_enable": (None, [ctypes.c_int]),
@@ -368,6 +369,11 @@ def join_materialize_into(A: Table, B: Table, out_a, out_b, total, ws, stream=No
     _check(load().hg_join_materialize(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(out_a),
                                       _ptr(out_b), out_a.numel(), _ptr(total), _ptr(ws), ws.numel(),
                                       _stream_handle(stream)), "hg_join_materialize")
+
+
+def selftest_wait_timeout(ws, limit_ms: int = 50, stream=None):
+    """Run the bounded-wait self-test (hg_selftest_wait_timeout) on ws."""
+    _check(load().hg_selftest_wait_timeout(_ptr(ws), limit_ms, _stream_handle(stream)), "hg_selftest_wait_timeout")
 
 
 def workspace_status(ws, stream=None) -> int:

@@ -245,6 +245,28 @@ hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_
   });
 }
 
+// One CTA waits on a barrier initialised for two arrivals that only ever
+// gets one: the bounded wait gives up after limit_ns, records
+// HG_ERR_TIMEOUT and the kernel returns.
+__global__ void k_selftest_wait(uint32_t* status, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive(&bar);
+  mbar_wait_block(&bar, 0, status, limit_ns);
+}
+
+hg_status hg_selftest_wait_timeout(void* d_ws, uint32_t limit_ms, void* stream) {
+  if (!d_ws || limit_ms == 0 || limit_ms > 5000) return HG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+  k_selftest_wait<<<1, 64, 0, st>>>(&((WsHeader*)d_ws)->status, (uint64_t)limit_ms * 1000000ull);
+  return last_launch_status();
+}
+
 hg_status hg_workspace_status(const void* d_ws, void* stream) {
   if (!d_ws) return HG_ERR_INVALID_ARG;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return HG_ERR_CUDA;

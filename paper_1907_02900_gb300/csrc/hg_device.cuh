@@ -394,6 +394,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_fence_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                "r"(bytes)
@@ -424,7 +427,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // HG_ERR_TIMEOUT, waits once more (bounded) so that no copy is still landing
 // in shared memory, and the caller must return.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
-__device__ __forceinline__ bool mbar_wait_block(uint64_t* bar, uint32_t parity, uint32_t* status) {
+__device__ __forceinline__ bool mbar_wait_block(uint64_t* bar, uint32_t parity, uint32_t* status,
+                                                uint64_t limit_ns = kWaitLimitNs) {
   bool ok = mbar_try_wait(bar, parity);
   if (!ok) {
     const uint64_t t0 = globaltimer_ns();
@@ -433,14 +437,14 @@ __device__ __forceinline__ bool mbar_wait_block(uint64_t* bar, uint32_t parity, 
         ok = true;
         break;
       }
-      if ((it & 255u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) break;
+      if ((it & 255u) == 0 && globaltimer_ns() - t0 > limit_ns) break;
     }
   }
   ok = __syncthreads_and(ok);
   if (!ok) {
     set_status(status, HG_ERR_TIMEOUT);
     const uint64_t t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t0 < kWaitLimitNs) {
+    while (!mbar_try_wait(bar, parity) && globaltimer_ns() - t0 < limit_ns) {
     }
   }
   return ok;
