@@ -62,7 +62,13 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
 #pragma unroll
     for (int k = 0; k < QPT; ++k) {
       uint32_t cnt = (s[k] < e[k] && first[k] == key[k]) ? 1u : 0u;
-      for (uint32_t j = s[k] + 1; j < e[k]; ++j) cnt += __ldg(ck + j) == key[k];
+      uint32_t j = s[k] + 1;
+      // four independent loads in flight per round for long buckets
+      for (; j + 4 <= e[k]; j += 4) {
+        const K a0 = __ldg(ck + j), a1 = __ldg(ck + j + 1), a2 = __ldg(ck + j + 2), a3 = __ldg(ck + j + 3);
+        cnt += (a0 == key[k]) + (a1 == key[k]) + (a2 == key[k]) + (a3 == key[k]);
+      }
+      for (; j < e[k]; ++j) cnt += __ldg(ck + j) == key[k];
       c[k] = cnt;
     }
 #pragma unroll
