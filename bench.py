@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--hit", type=float, default=0.5)
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--standard-probe", action="store_true", help="time HashGraph-Probe-Standard instead of the binned probe")
+    ap.add_argument("--algo", choices=["v2", "v1"], default="v2", help="build algorithm (Alg. 2 or Alg. 1)")
+    ap.add_argument("--explicit-ids", action="store_true", help="build with a uint32 id array (+4 B read per key)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
     ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed runs of the per-table loop")
@@ -375,7 +377,11 @@ def run_scale(c: Ctx):
     del keys_h, q_h
     keys_d = keys_p.to(c.dev).view(torch.uint32)
     q_d = q_p.to(c.dev).view(torch.uint32)
-    cfg = hg.make_config(hg.KEY_U32, V, 0, "v2")
+    cfg = hg.make_config(hg.KEY_U32, V, 0, args.algo)
+    ids_d = None
+    if args.explicit_ids:   # a permutation-like id array: ids = position * odd constant (mod 2^32)
+        ids_d = (torch.arange(n, dtype=torch.int64, device=c.dev) * 2654435761 % (1 << 32)).to(torch.int32).view(
+            torch.uint32)
     ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=c.dev)
     offsets = torch.empty(V + 1, dtype=torch.uint32, device=c.dev)
     ck = torch.empty(n, dtype=torch.uint32, device=c.dev)
@@ -386,7 +392,7 @@ def run_scale(c: Ctx):
     pws = torch.empty(max(hg.probe_workspace_size(table, q), 1), dtype=torch.uint8, device=c.dev) if binned else None
 
     def step(kd, qd):
-        hg.build_into(cfg, kd, None, offsets, ck, ci, ws, c.stream)
+        hg.build_into(cfg, kd, ids_d, offsets, ck, ci, ws, c.stream)
         if binned:
             hg.probe_binned_into(table, qd, counts, pws, c.stream)
         else:
@@ -402,6 +408,11 @@ def run_scale(c: Ctx):
     value, elapsed_ms = c.rate((n + q) * args.steps, local_ms)
     ms_per_step = elapsed_ms / args.steps
     algo = dict(algo_build(4, n, V), **algo_probe(4, n, V, q, args.hit, binned))
+    if args.explicit_ids:
+        algo["k_partition_A"] += 4 * n        # the id array is read too
+    if args.algo == "v1":
+        for k in ("k_hist", "k_partition_A", "k_partition_B", "k_binbuild"):
+            algo.pop(k)
     units = {k: (q if k in PROBE_KERNELS else n) for k in algo}
     roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
     build_ms = sum(prof[k][0] for k in prof if k not in PROBE_KERNELS) / args.steps
@@ -465,7 +476,9 @@ def run_scale(c: Ctx):
         secs, done = oracle_sample(ln, lv, args.hit, seed + 7)
         cpu = cpu_line(secs, done, f"oracle build of 2^{ln} uint32 keys into 2^{lv} buckets + probe of 2^{ln} "
                                    f"queries ({int(args.hit * 100)}% hits)")
-    config = {"workload": f"HashGraph-V2 build of 2^{args.log2n} uniform uint32 keys (implicit ids) into 2^{log2v} "
+    algo_name = "HashGraph-V2" if args.algo == "v2" else "HashGraph-V1"
+    ids_name = "explicit uint32 ids" if args.explicit_ids else "implicit ids"
+    config = {"workload": f"{algo_name} build of 2^{args.log2n} uniform uint32 keys ({ids_name}) into 2^{log2v} "
                           f"buckets (murmur3) + {'binned probe' if binned else 'Probe-Standard'} of 2^{args.log2n} "
                           f"queries at {int(args.hit * 100)}% hits, per GPU",
               "global_batch": c.world * (n + q),

@@ -1023,7 +1023,9 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   {
     HG_TRACE("k_scan_bins", st);
     HugeArgs h{};
-    h.list = (uint32_t*)(ws + p.o_hlist);
+    // below kHugeMinN keys every oversized bin goes to the one-CTA path (at
+    // most a few million edges), which spares small builds three launches
+    if (p.n >= kHugeMinN) h.list = (uint32_t*)(ws + p.o_hlist);
     h.count = (uint32_t*)&hdr->counters[0];
     h.rows = (uint32_t*)&hdr->counters[0] + 1;
     h.rowdesc = (uint32_t*)(ws + p.o_rowdesc);
@@ -1129,7 +1131,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
       kern<<<grid, kBinNW * 32, sm, st>>>(ba, ovf, &hdr->ovf_count, map);
     }
   }
-  if (p.n > kHugeSeg) {
+  if (p.n >= kHugeMinN) {
     // bins above kHugeSeg edges (duplicates): several CTAs per bin
     const uint32_t nbmax = 1u << p.s;
     uint32_t* hcount = (uint32_t*)&hdr->counters[0];
@@ -1396,8 +1398,10 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
                                       Map::kNeedsPos ? qi : nullptr);
   if (rc != HG_OK) return rc;
   {
-    const uint64_t tiles = (q + kUnpermuteTile - 1) / kUnpermuteTile;
-    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)2 * di.sms));
+    // every CTA merges a span of at least 4096 outputs (in tiles of up to
+    // kUnpermuteTile), so small batches still spread over the SMs
+    const uint64_t spans = (q + 4095) / 4096;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(spans, (uint64_t)2 * di.sms));
     const uint64_t span = (q + grid - 1) / grid;
     HG_TRACE("k_unpermute", st);
     if (Map::kNeedsPos)

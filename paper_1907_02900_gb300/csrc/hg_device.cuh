@@ -155,31 +155,36 @@ struct LearnedMap {
   static constexpr bool kNeedsPos = false;
   const uint8_t* blob;  // device pointer
   uint64_t Vcap;        // buckets of the table being built (host-provided bound)
-  float a, b;
+  float a, b, Lf;
   uint32_t L;
-  uint64_t V;
+  uint64_t V, vmax;
   const LearnedLeaf* leaves;
   __device__ __forceinline__ void init() {
     L = __ldg((const uint32_t*)(blob + 4));
     V = __ldg((const unsigned long long*)(blob + 8));
     a = __ldg((const float*)(blob + 16));
     b = __ldg((const float*)(blob + 20));
+    Lf = __uint2float_rn(L);
+    vmax = V < Vcap ? V : Vcap;
     leaves = (const LearnedLeaf*)(blob + kModelHeaderBytes);
   }
   template <typename K>
   __device__ __forceinline__ uint32_t leaf_of(K key) const {
     float r = __fadd_rn(__fmul_rn(a, rmi_feature(key)), b);
     if (!(r >= 0.0f)) return 0;
-    if (r >= __uint2float_rn(L)) return L - 1;
+    if (r >= Lf) return L - 1;
     return (uint32_t)r;
   }
   __device__ __forceinline__ uint32_t out_id(uint32_t id) const { return id; }
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
-    const LearnedLeaf* lf = leaves + leaf_of(key);
-    uint64_t xmin = __ldg((const unsigned long long*)&lf->xmin);
-    float slope = __ldg(&lf->slope), icpt = __ldg(&lf->icpt);
-    uint32_t base = __ldg(&lf->base), width = __ldg(&lf->width);
+    // a leaf record is 24 bytes at an 8-byte boundary: three 8-byte loads
+    const unsigned long long* rec = (const unsigned long long*)(leaves + leaf_of(key));
+    const uint64_t xmin = __ldg(rec);
+    const float2 si = __ldg((const float2*)(rec + 1));
+    const uint2 bw = __ldg((const uint2*)(rec + 2));
+    const float slope = si.x, icpt = si.y;
+    const uint32_t base = bw.x, width = bw.y;
     uint32_t local = 0;
     if (width > 0) {
       uint64_t k = (uint64_t)key;
@@ -189,7 +194,6 @@ struct LearnedMap {
       else if (p >= __uint2float_rn(width)) local = width - 1;
       else local = min((uint32_t)p, width - 1);
     }
-    const uint64_t vmax = V < Vcap ? V : Vcap;
     const uint64_t bk = (uint64_t)base + local;
     return (uint32_t)(bk < vmax ? bk : vmax - 1);
   }

@@ -62,10 +62,10 @@ def test_build_all_keys_equal_and_single_bucket(hg, orc):
 
 @pytest.mark.parametrize("kt", ["u32", "u64"])
 def test_build_huge_bins_split_across_ctas(hg, orc, kt):
-    # Two keys hold 40% and 20% of 2^21 keys: their bins exceed 2^17 edges and
+    # Two keys hold 40% and 20% of 2^22 keys: their bins exceed 2^17 edges and
     # are built by several CTAs, one per 2^17-edge segment; the rest of the
     # table stays on the shared-memory path.
-    n = 1 << 21
+    n = 1 << 22
     base = dg.uniform_keys_u32(n, 21) if kt == "u32" else dg.uniform_keys_u64(n, 21)
     sel = dg.splitmix64(21, 99, np.arange(n, dtype=np.uint64)) >> np.uint64(11)
     u = sel.astype(np.float64) / float(1 << 53)
@@ -76,10 +76,10 @@ def test_build_huge_bins_split_across_ctas(hg, orc, kt):
         _check_build(hg, orc, keys, 1 << 20, algo=algo)
 
 
-@pytest.mark.parametrize("n", [3 << 17, (3 << 17) + 1, 1 << 20])
+@pytest.mark.parametrize("n", [1 << 22, (1 << 22) + 1, (1 << 22) + (5 << 17) - 3])
 def test_build_single_bucket_segment_edges(hg, orc, n):
-    # one bin, one bucket: exactly k segments, k segments plus one edge, and
-    # 2^20 equal keys
+    # one bin, one bucket: exactly 32 segments, 32 segments plus one edge, a
+    # ragged last segment; and the same number of equal keys
     keys = dg.uniform_keys_u32(n, 5)
     _check_build(hg, orc, keys, 1, algo="v2")
     _check_build(hg, orc, np.full(n, 77, dtype=np.uint32), 1 << 12, algo="v2")
