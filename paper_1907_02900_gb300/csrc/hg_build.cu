@@ -35,14 +35,6 @@ static int ceil_log2_u64(uint64_t x) {
   return l;
 }
 
-size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf) {
-  // staging buffers of keys and ids, lb and slot arrays (u16), packed u16
-  // bucket counters, heavy-bucket list, list of buckets with two or more edges
-  size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + 2 * (size_t)emax * 2 + (((size_t)1 << s) + 1) / 2 * 4 +
-             ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2 + ((size_t)emax / 2 + 2) * 2;
-  return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
-}
-
 // stream_runs' shared memory after the cursors: tile keys and ids, four u16
 // tile arrays, the ranking counters and a scan scratch (last 128 bytes)
 __host__ __device__ inline size_t big_rest_bytes(int kb) {
@@ -67,7 +59,7 @@ bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p) {
   p->n = n;
   p->V = cfg->num_buckets;
   p->emax = p->kb == 4 ? kBinEmaxU32 : kBinEmaxU64;
-  p->tpb = cfg->threads_per_bin == 512 ? 512u : 1024u;
+  p->tpb = cfg->threads_per_bin;  // 0 (automatic), 512 or 1024
   const uint64_t V = p->V;
   int s;
   if (cfg->bin_shift) {
@@ -293,19 +285,14 @@ template <typename K, typename Map, bool PASS_B, int IPT, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map map) {
   constexpr uint32_t TILE = NW * 32 * IPT;
   constexpr uint32_t TB = TILE + 16;
+  static_assert(TILE <= 65536, "tile indexes are packed into 16 bits");
   const bool has_ids = PASS_B || a.in_i != nullptr;
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sp = smem;
-  K* kin[2];
-  uint32_t* iin[2];
-  kin[0] = (K*)sp; sp += TB * sizeof(K);
-  kin[1] = (K*)sp; sp += TB * sizeof(K);
-  if (has_ids) {
-    iin[0] = (uint32_t*)sp; sp += TB * 4;
-    iin[1] = (uint32_t*)sp; sp += TB * 4;
-  } else {
-    iin[0] = iin[1] = nullptr;
-  }
+  // staging buffer b of keys at kin0 + b * TB, of ids at iin0 + b * TB
+  K* const kin0 = (K*)sp; sp += 2 * TB * sizeof(K);
+  uint32_t* const iin0 = has_ids ? (uint32_t*)sp : nullptr;
+  if (has_ids) sp += 2 * TB * 4;
   K* sk = (K*)sp; sp += TILE * sizeof(K);
   uint32_t* sv = (uint32_t*)sp; sp += TILE * 4;
   uint32_t* wc = (uint32_t*)sp; sp += rank_words<NW>() * 4;
@@ -333,34 +320,36 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
       ihi[j] = base + (g1 < a.G ? a.C[(uint64_t)g1 * a.nsb + sb] : a.CT[sb]);
     }
   }
-  auto item_range = [&](uint64_t item, uint64_t& i0, uint64_t& i1) {
+  // This CTA's items are blockIdx.x + j * gridDim.x for j = 0, 1, ...; the
+  // tile stream walks them by j (32-bit), tiles of TILE elements.
+  const uint32_t nmine = blockIdx.x < nitems ? (uint32_t)((nitems - blockIdx.x + gridDim.x - 1) / gridDim.x) : 0u;
+  auto item_range = [&](uint32_t j, uint64_t& i0, uint64_t& i1) {
     if (!PASS_B) {
-      i0 = item * a.chunk;
+      i0 = ((uint64_t)blockIdx.x + (uint64_t)j * gridDim.x) * a.chunk;
       i1 = min(i0 + a.chunk, a.n);
     } else {
-      const uint64_t j = (item - blockIdx.x) / gridDim.x;
       i0 = ilo[j];
       i1 = ihi[j];
     }
   };
-  // Tile stream of this CTA: items blockIdx.x, +gridDim.x, ...; tiles of TILE.
   struct Ref {
-    uint64_t item, t0, t1;
+    uint32_t j;
     bool ok;
+    uint64_t t0, t1;
   };
-  auto first_from = [&](uint64_t item) -> Ref {
-    for (; item < nitems; item += gridDim.x) {
+  auto first_from = [&](uint32_t j) -> Ref {
+    for (; j < nmine; ++j) {
       uint64_t i0, i1;
-      item_range(item, i0, i1);
-      if (i1 > i0) return Ref{item, i0, min(i0 + TILE, i1), true};
+      item_range(j, i0, i1);
+      if (i1 > i0) return Ref{j, true, i0, min(i0 + TILE, i1)};
     }
-    return Ref{0, 0, 0, false};
+    return Ref{0, false, 0, 0};
   };
   auto next_of = [&](const Ref& r) -> Ref {
     uint64_t i0, i1;
-    item_range(r.item, i0, i1);
-    if (r.t1 < i1) return Ref{r.item, r.t1, min(r.t1 + TILE, i1), true};
-    return first_from(r.item + gridDim.x);
+    item_range(r.j, i0, i1);
+    if (r.t1 < i1) return Ref{r.j, true, r.t1, min(r.t1 + TILE, i1)};
+    return first_from(r.j + 1);
   };
   auto issue = [&](const Ref& r, int buf) {
     if (threadIdx.x == 0) {
@@ -372,8 +361,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
         bytes += si_.bytes();
       }
       mbar_arrive_expect_tx(&bar[buf], bytes);
-      if (sk_.body) tma_load_1d(kin[buf], a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
-      if (has_ids && si_.body) tma_load_1d(iin[buf], a.in_i + si_.a0, si_.bytes(), &bar[buf]);
+      if (sk_.body) tma_load_1d(kin0 + buf * TB, a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
+      if (has_ids && si_.body) tma_load_1d(iin0 + buf * TB, a.in_i + si_.a0, si_.bytes(), &bar[buf]);
     }
   };
 
@@ -384,10 +373,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
   }
   __syncthreads();
 
-  Ref cur = first_from(blockIdx.x);
+  Ref cur = first_from(0);
   if (!cur.ok) return;
   issue(cur, 0);
-  uint64_t cur_item = ~0ull;
+  uint32_t cur_j = ~0u, sb = 0;
   int ndig = 0;
   const uint32_t seg0 = (threadIdx.x >> 5) * (32u * IPT), lane = lane_id();
   for (uint32_t it = 0; cur.ok; ++it) {
@@ -401,18 +390,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
     // elements past the last 16-byte boundary (only where a tile ends
     // unaligned) come in by plain loads; the barrier is needed only then
     bool sync_needed = (sk_.a0 + sk_.body < cur.t1) || (has_ids && si_.a0 + si_.body < cur.t1);
-    load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
-    if (has_ids) load_tail<4>(iin[buf], a.in_i, si_);
-    uint32_t sb = 0;
-    if (PASS_B) sb = (uint32_t)(cur.item / a.ngroups);
-    if (cur.item != cur_item) {  // cursors are first read after tile_partition_fast's first barrier
-      cur_item = cur.item;
+    load_tail<sizeof(K)>(kin0 + buf * TB, a.in_k, sk_);
+    if (has_ids) load_tail<4>(iin0 + buf * TB, a.in_i, si_);
+    if (cur.j != cur_j) {  // cursors are first read after tile_partition_fast's first barrier
+      cur_j = cur.j;
+      const uint32_t item = blockIdx.x + cur.j * gridDim.x;
       if (!PASS_B) {
         ndig = (int)a.nsb;
         for (int d = threadIdx.x; d < ndig; d += blockDim.x)
-          cursor[d] = a.BS[(uint32_t)d << a.sshift] + a.C[cur.item * a.nsb + d];
+          cursor[d] = a.BS[(uint32_t)d << a.sshift] + a.C[(uint64_t)item * a.nsb + d];
       } else {
-        const uint32_t g = (uint32_t)(cur.item % a.ngroups) * a.gg;
+        sb = item / a.ngroups;
+        const uint32_t g = (item - sb * a.ngroups) * a.gg;
         const uint32_t b0 = sb << a.sshift;
         ndig = (int)min(1u << a.sshift, a.nbins - b0);
         for (int d = threadIdx.x; d < ndig; d += blockDim.x)
@@ -421,8 +410,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
     }
     if (sync_needed) __syncthreads();  // block-uniform condition
     const uint32_t cnt = (uint32_t)(cur.t1 - cur.t0);
-    const K* kk = kin[buf] + (cur.t0 - sk_.a0);
-    const uint32_t* ii = has_ids ? iin[buf] + (cur.t0 - si_.a0) : nullptr;
+    const K* kk = kin0 + buf * TB + (cur.t0 - sk_.a0);
+    const uint32_t* ii = has_ids ? iin0 + buf * TB + (cur.t0 - si_.a0) : nullptr;
     K key[IPT];
     uint32_t val[IPT], dig[IPT];
 #pragma unroll
@@ -430,8 +419,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
       const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
       if (idx < cnt) {
         key[r] = kk[idx];
-        val[r] = has_ids ? ii[idx] : (uint32_t)(cur.t0 + idx);
-        const uint32_t bucket = map(key[r], val[r]);
+        val[r] = has_ids ? ii[idx] : idx;
+        const uint32_t bucket = map(key[r], has_ids ? val[r] : (uint32_t)(cur.t0 + idx));
         dig[r] = PASS_B ? (bucket >> a.s) - (sb << a.sshift) : bucket >> (a.s + a.sshift);
       } else {
         key[r] = 0;
@@ -439,15 +428,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
         dig[r] = 0;
       }
     }
-    tile_partition_fast<K, IPT, NW>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
-                                    a.out_k, a.out_i);
+    if (has_ids)
+      tile_partition_fast<K, IPT, NW, false>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                             a.out_k, a.out_i, 0u);
+    else
+      tile_partition_fast<K, IPT, NW, true>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                            a.out_k, a.out_i, (uint32_t)cur.t0);
     cur = nxt;
   }
 }
 
-// Phase 3: build every bin in shared memory.  Persistent CTAs (one per SM)
-// take bins round-robin; the next bin's keys and ids are fetched by TMA
-// while the current one is sorted.  Bins above emax are skipped here.
+// Phase 3: build every bin in shared memory.  Persistent CTAs (one or two
+// per SM) take bins round-robin; with two staging buffers the next bin's
+// keys and ids are fetched by TMA while the current one is sorted.  Bins
+// above emax are skipped here.
 template <typename K>
 struct BinArgs {
   const K* in_k;
@@ -464,39 +458,69 @@ struct BinArgs {
   uint32_t* status;
 };
 
+// Whether the bin build recomputes an edge's bucket rather than keeping it
+// in shared memory between its two uses (cheap maps only).
+template <typename Map>
+struct recompute_bucket {
+  static constexpr bool value = false;
+};
+template <>
+struct recompute_bucket<MurmurMap> {
+  static constexpr bool value = true;
+};
+
+// Warps that sort long buckets with position bitmaps: with a local-bucket
+// array its space holds sixteen bitmaps once it is dead; without one, four
+// bitmaps get their own space.
+template <bool LB>
+__host__ __device__ constexpr uint32_t bin_bitmap_warps() {
+  return LB ? kBinBitmapWarps : 4u;
+}
+
+// Shared memory of k_binbuild: staging buffers of keys and ids, the local
+// bucket array (LB), slot order (u16), packed u16 bucket counters, the list
+// of long buckets, the bitmaps (without LB) and small control state.
+size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
+  size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + (lb ? (size_t)emax * 2 : 0) + (size_t)emax * 2 +
+             (((size_t)1 << s) + 1) / 2 * 4 + ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2;
+  b = align_up(b, 16);
+  if (!lb) b += (size_t)bin_bitmap_warps<false>() * (emax / 32 + 1) * 4;
+  return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
+}
+
 // Per bin (E <= emax edges, nb local buckets):
-//   1. local bucket lb of every edge; bucket counts by shared-memory atomics
+//   1. local bucket of every edge; bucket counts by shared-memory atomics
 //      (counts do not depend on order); two 16-bit counters per word
-//   2. exclusive scan of the counts -> the bin's CSR offsets (written out)
+//   2. exclusive scan of the counts -> bucket starts, packed the same way
 //   3. every edge claims a slot of its bucket with an atomic increment; the
 //      slot order inside a bucket is arbitrary at this point
 //   4. every bucket sorts its slots by position in the bin, which is input
 //      order because both partition passes are stable: insertion sort for
 //      up to kBinSmallBucket edges, a per-warp position bitmap above
-//   5. the edges are written out in slot order (coalesced)
-template <typename K, typename Map, int NWB>
-__global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map) {
+//   5. the edges are written out in slot order, and the bin's offsets
+//      (both coalesced)
+// LB: the local buckets of step 1 are kept for step 3 (else recomputed).
+template <typename K, typename Map, int NWB, int MINB, bool LB>
+__global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map map) {
+  constexpr uint32_t NBM = bin_bitmap_warps<LB>();
   const uint32_t EB = a.emax + 16;
   const int nbuf = a.nbuf;
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sp = smem;
-  K* kin[2];
-  uint32_t* iin[2];
-  kin[0] = (K*)sp; sp += (size_t)EB * sizeof(K);
-  kin[1] = kin[0];
-  if (nbuf == 2) { kin[1] = (K*)sp; sp += (size_t)EB * sizeof(K); }
-  iin[0] = (uint32_t*)sp; sp += (size_t)EB * 4;
-  iin[1] = iin[0];
-  if (nbuf == 2) { iin[1] = (uint32_t*)sp; sp += (size_t)EB * 4; }
-  uint16_t* lb = (uint16_t*)sp; sp += (size_t)a.emax * 2;        // also the heavy-bucket bitmaps
+  // staging buffer b of keys at kin0 + b * EB, of ids at iin0 + b * EB
+  K* const kin0 = (K*)sp; sp += (size_t)nbuf * EB * sizeof(K);
+  uint32_t* const iin0 = (uint32_t*)sp; sp += (size_t)nbuf * EB * 4;
+  uint16_t* lb = (uint16_t*)sp; sp += LB ? (size_t)a.emax * 2 : 0;
   uint16_t* opos = (uint16_t*)sp; sp += (size_t)a.emax * 2;
   uint32_t* cnt = (uint32_t*)sp; sp += (((size_t)1 << a.s) + 1) / 2 * 4;
   uint16_t* heavy = (uint16_t*)sp; sp += (size_t)(a.emax / (kBinSmallBucket + 1) + 2) * 2;
-  uint16_t* multi = (uint16_t*)sp; sp += (size_t)(a.emax / 2 + 2) * 2;  // buckets holding >= 2 edges
+  sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
+  const uint32_t bm_words = (a.emax + 31) / 32;  // emax is a multiple of 32 when LB
+  uint32_t* bitmaps = LB ? (uint32_t*)lb : (uint32_t*)sp;  // NBM bitmaps of bm_words words
+  if (!LB) sp += (size_t)NBM * bm_words * 4;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
-  uint32_t* nheavy = (uint32_t*)sp; sp += 16;  // [0] heavy buckets, [1] entries of multi
-  uint32_t* nmulti = nheavy + 1;
+  uint32_t* nheavy = (uint32_t*)sp; sp += 16;
   uint32_t* bl_start = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;  // this CTA's bins: start, size
   uint32_t* bl_size = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;
   uint64_t* bar = (uint64_t*)sp;
@@ -521,8 +545,8 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
       const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(k0, k1);
       const TileSpan<4> si_ = tile_span<4>(k0, k1);
       mbar_arrive_expect_tx(&bar[buf], sk_.bytes() + si_.bytes());
-      if (sk_.body) tma_load_1d(kin[buf], a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
-      if (si_.body) tma_load_1d(iin[buf], a.in_i + si_.a0, si_.bytes(), &bar[buf]);
+      if (sk_.body) tma_load_1d(kin0 + (size_t)buf * EB, a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
+      if (si_.body) tma_load_1d(iin0 + (size_t)buf * EB, a.in_i + si_.a0, si_.bytes(), &bar[buf]);
     }
   };
   if (threadIdx.x == 0) {
@@ -544,85 +568,87 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
     const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
     const uint32_t nwords = (nb + 1) >> 1;
     for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) cnt[w] = 0;
-    if (threadIdx.x == 0) {
-      *nheavy = 0;
-      *nmulti = 0;
-    }
+    if (threadIdx.x == 0) *nheavy = 0;
     const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
     if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
     const uint32_t E = bl_size[jb], start = bl_start[jb];
     const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(start, (uint64_t)start + E);
     const TileSpan<4> si_ = tile_span<4>(start, (uint64_t)start + E);
-    load_tail<sizeof(K)>(kin[buf], a.in_k, sk_);
-    load_tail<4>(iin[buf], a.in_i, si_);
+    K* const kb_ = kin0 + (size_t)buf * EB;
+    uint32_t* const ib_ = iin0 + (size_t)buf * EB;
+    load_tail<sizeof(K)>(kb_, a.in_k, sk_);
+    load_tail<4>(ib_, a.in_i, si_);
     if (sk_.a0 + sk_.body < (uint64_t)start + E || si_.a0 + si_.body < (uint64_t)start + E)
       __syncthreads();  // tail elements came in by plain loads (block-uniform condition)
-    const K* kk = kin[buf] + (start - sk_.a0);
-    const uint32_t* ii = iin[buf] + (start - si_.a0);
+    const K* kk = kb_ + (start - sk_.a0);
+    const uint32_t* ii = ib_ + (start - si_.a0);
     // 1. local buckets and counts
     for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
       const uint32_t l = map(kk[e], ii[e]) - (uint32_t)bucket0;
-      lb[e] = (uint16_t)l;
+      if (LB) lb[e] = (uint16_t)l;
       atomicAdd(&cnt[l >> 1], 1u << ((l & 1u) << 4));
     }
     __syncthreads();
-    // 2. exclusive scan of the counts; offsets of the bin's buckets
+    // 2. exclusive scan of the counts; every thread keeps its word range
+    const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
+    const uint32_t w0 = min(threadIdx.x * per, nwords), w1 = min(w0 + per, nwords);
     {
-      const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
-      const uint32_t w0 = threadIdx.x * per, w1 = min(w0 + per, nwords);
-      uint32_t s = 0;
+      uint32_t sum = 0;
       for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t x = cnt[w];
-        s += (x & 0xffffu) + (x >> 16);
+        sum += (x & 0xffffu) + (x >> 16);
       }
-      uint32_t base = block_excl_scan_nt<uint32_t>(s, wsum);
+      uint32_t base = block_excl_scan_nt<uint32_t>(sum, wsum);
       for (uint32_t w = w0; w < w1; ++w) {
-        const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
-        const uint32_t v = 2 * w;
-        a.offsets[bucket0 + v] = a.pos_base + start + base;
-        if (v + 1 < nb) a.offsets[bucket0 + v + 1] = a.pos_base + start + base + lo;
-        if (lo > 1) multi[atomicAdd(nmulti, 1u)] = (uint16_t)v;
-        if (hi > 1) multi[atomicAdd(nmulti, 1u)] = (uint16_t)(v + 1);
+        const uint32_t x = cnt[w], lo = x & 0xffffu;
         cnt[w] = base | ((base + lo) << 16);
-        base += lo + hi;
+        base += lo + (x >> 16);
       }
     }
     __syncthreads();
     // 3. slots
     for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
-      const uint32_t l = lb[e], sh = (l & 1u) << 4;
+      const uint32_t l = LB ? (uint32_t)lb[e] : map(kk[e], ii[e]) - (uint32_t)bucket0;
+      const uint32_t sh = (l & 1u) << 4;
       const uint32_t old = atomicAdd(&cnt[l >> 1], 1u << sh);
       opos[(old >> sh) & 0xffffu] = (uint16_t)e;
     }
     __syncthreads();
-    // 4. order inside each bucket of two or more edges: ascending position
-    const uint32_t nm = *nmulti;
-    for (uint32_t i = threadIdx.x; i < nm; i += blockDim.x) {
-      const uint32_t v = multi[i];
-      const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
-      const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
-      const uint32_t c = end - beg;
-      if (c <= kBinSmallBucket) {
-        for (uint32_t k = beg + 1; k < end; ++k) {
-          const uint16_t p = opos[k];
-          uint32_t j = k;
-          while (j > beg && opos[j - 1] > p) {
-            opos[j] = opos[j - 1];
-            --j;
+    // 4. order inside each bucket of two or more edges (every counter now
+    //    holds its bucket's end): this thread's buckets 2*w0 .. 2*w1-1
+    {
+      uint32_t prev = w0 ? cnt[w0 - 1] >> 16 : 0u;  // end of bucket 2*w0 - 1
+      for (uint32_t w = w0; w < w1; ++w) {
+        const uint32_t x = cnt[w];
+        const uint32_t ends[2] = {x & 0xffffu, x >> 16};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t beg = prev, end = ends[h];
+          prev = end;
+          if (end - beg < 2) continue;
+          if (end - beg <= kBinSmallBucket) {
+            for (uint32_t k = beg + 1; k < end; ++k) {
+              const uint16_t p = opos[k];
+              uint32_t j = k;
+              while (j > beg && opos[j - 1] > p) {
+                opos[j] = opos[j - 1];
+                --j;
+              }
+              opos[j] = p;
+            }
+          } else {
+            heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + h);
           }
-          opos[j] = p;
         }
-      } else {
-        heavy[atomicAdd(nheavy, 1u)] = (uint16_t)v;
       }
     }
     __syncthreads();
     const uint32_t nh = *nheavy;
-    if (nh > 0 && warp < kBinBitmapWarps) {
-      // lb is dead: each of the first kBinBitmapWarps warps owns emax bits of it
+    if (nh > 0 && warp < NBM) {
+      // each of the first NBM warps owns one bitmap of E bits
       const uint32_t nbits_words = (E + 31) >> 5;
-      uint32_t* bm = (uint32_t*)lb + warp * (a.emax >> 5);
-      for (uint32_t h = warp; h < nh; h += kBinBitmapWarps) {
+      uint32_t* bm = bitmaps + warp * bm_words;
+      for (uint32_t h = warp; h < nh; h += NBM) {
         const uint32_t v = heavy[h];
         const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
         const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
@@ -650,16 +676,70 @@ __global__ void __launch_bounds__(NWB * 32, 1) k_binbuild(BinArgs<K> a, Map map)
       }
     }
     if (nh > 0) __syncthreads();  // block-uniform: every thread read the same count
-    // 5. edges in bucket order
+    // 5. edges in bucket order; the bin's offsets (bucket v starts where
+    //    bucket v - 1 ends)
     for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
       const uint32_t p = opos[j];
       a.csr_k[start + j] = kk[p];
       a.csr_i[start + j] = map.out_id(ii[p]);
     }
+    for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
+      const uint32_t first = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
+      a.offsets[bucket0 + v] = a.pos_base + start + first;
+    }
     __syncthreads();
     if (nbuf == 1 && jb_next < nmine) issue(jb_next, 0);
     jb = jb_next;
   }
+}
+
+// Bin-build launch configuration: 512-thread CTAs two to an SM, single
+// buffered, when two fit with bins large enough for this build; otherwise
+// one CTA per SM (1024 threads unless 512 were asked for), double buffered
+// when that fits.
+struct BinCfg {
+  uint32_t tpb, per_sm, emax;
+  int nbuf;
+  bool lb;
+  size_t smem;
+};
+#ifndef HG_BIN_TWO_PER_SM
+#define HG_BIN_TWO_PER_SM 1
+#endif
+static BinCfg bin_config(const Plan& p, bool recompute) {
+  const DevInfo& di = dev_info();
+  BinCfg c{};
+  if (HG_BIN_TWO_PER_SM && p.tpb != 1024 && di.smem_per_sm > 0) {
+    const bool lb = !recompute;
+    const double mean = p.nbins ? (double)p.n / (double)p.nbins : 0.0;
+    const size_t sm_cap = (size_t)di.smem_per_sm / 2 - (size_t)di.smem_reserved;
+    uint32_t e = p.emax;
+    // (multiples of 32, so that the sixteen bitmaps fit in the local-bucket array)
+    while (e > 1024 && (bin_smem_bytes(p.kb, e, p.s, 1, lb) > sm_cap ||
+                        bin_smem_bytes(p.kb, e, p.s, 1, lb) > (size_t)di.max_smem_optin))
+      e -= 32;
+    // bins of a uniform build are Poisson: allow five standard deviations
+    if (bin_smem_bytes(p.kb, e, p.s, 1, lb) <= sm_cap && (double)e >= mean + 5.0 * std::sqrt(mean) + 16.0) {
+      c.tpb = 512;
+      c.per_sm = 2;
+      c.emax = e;
+      c.nbuf = 1;
+      c.lb = lb;
+      c.smem = bin_smem_bytes(p.kb, e, p.s, 1, lb);
+      return c;
+    }
+  }
+  c.tpb = p.tpb == 512 ? 512u : 1024u;
+  c.per_sm = 1;
+  c.emax = p.emax;
+  c.lb = true;
+  c.nbuf = 2;
+  c.smem = bin_smem_bytes(p.kb, p.emax, p.s, 2, true);
+  if (c.smem > (size_t)di.max_smem_optin) {
+    c.nbuf = 1;
+    c.smem = bin_smem_bytes(p.kb, p.emax, p.s, 1, true);
+  }
+  return c;
 }
 
 // Streams edges [start, start + len) of a bin in tiles of kBigTile, sorts
@@ -1020,6 +1100,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     k_colscan<<<(p.nsb + 255) / 256, 256, 0, st>>>(C, p.G, p.nsb, CT);
   }
   const bool two = p.sshift > 0;
+  const BinCfg bc = bin_config(p, recompute_bucket<Map>::value);
   {
     HG_TRACE("k_scan_bins", st);
     HugeArgs h{};
@@ -1031,7 +1112,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     h.rowdesc = (uint32_t*)(ws + p.o_rowdesc);
     h.max_rows = p.max_rows;
     h.status = status;
-    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, p.emax, ovf, &hdr->ovf_count, offsets, p.V,
+    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, bc.emax, ovf, &hdr->ovf_count, offsets, p.V,
                                     pos_base + (uint32_t)p.n, h);
   }
 
@@ -1098,27 +1179,32 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   ba.V = p.V;
   ba.nbins = p.nbins;
   ba.s = p.s;
-  ba.emax = p.emax;
+  ba.emax = bc.emax;
   ba.pos_base = pos_base;
   ba.status = status;
+  ba.nbuf = bc.nbuf;
   {
-    size_t sm = bin_smem_bytes(sizeof(K), p.emax, p.s, 2);
-    ba.nbuf = 2;
-    if (sm > (size_t)di.max_smem_optin) {
-      sm = bin_smem_bytes(sizeof(K), p.emax, p.s, 1);
-      ba.nbuf = 1;
-    }
-    unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms);
+    unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms * bc.per_sm);
     grid = std::max<unsigned>(grid, (p.nbins + kMaxBinsPerCta - 1) / kMaxBinsPerCta);
     HG_TRACE("k_binbuild", st);
-    if (p.tpb == 512) {
-      auto kern = k_binbuild<K, Map, 16>;
-      set_smem_once(kern, sm);
-      kern<<<grid, 512, sm, st>>>(ba, map);
+    if (bc.per_sm == 2) {
+      if (bc.lb) {
+        auto kern = k_binbuild<K, Map, 16, 2, true>;
+        set_smem_once(kern, bc.smem);
+        kern<<<grid, 512, bc.smem, st>>>(ba, map);
+      } else {
+        auto kern = k_binbuild<K, Map, 16, 2, false>;
+        set_smem_once(kern, bc.smem);
+        kern<<<grid, 512, bc.smem, st>>>(ba, map);
+      }
+    } else if (bc.tpb == 512) {
+      auto kern = k_binbuild<K, Map, 16, 1, true>;
+      set_smem_once(kern, bc.smem);
+      kern<<<grid, 512, bc.smem, st>>>(ba, map);
     } else {
-      auto kern = k_binbuild<K, Map, kBinNW>;
-      set_smem_once(kern, sm);
-      kern<<<grid, kBinNW * 32, sm, st>>>(ba, map);
+      auto kern = k_binbuild<K, Map, kBinNW, 1, true>;
+      set_smem_once(kern, bc.smem);
+      kern<<<grid, kBinNW * 32, bc.smem, st>>>(ba, map);
     }
   }
   {

@@ -60,7 +60,7 @@ struct Plan {
   uint32_t G;        // input chunks of pass A
   uint64_t chunk;    // elements per chunk (multiple of 16)
   uint32_t emax;     // largest bin built in shared memory
-  uint32_t tpb;      // threads per bin-build CTA (512 or 1024)
+  uint32_t tpb;      // threads per bin-build CTA asked for (512 or 1024; 0 = automatic)
   uint32_t max_rows; // segments of huge bins (bins above kHugeSeg edges), upper bound
   size_t o_H, o_C, o_CT, o_T, o_BS, o_ovf, o_hlist, o_rowdesc, o_rowcnt, o_bk, o_bi, total;
 };

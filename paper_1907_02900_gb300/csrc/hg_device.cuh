@@ -298,6 +298,29 @@ __device__ __forceinline__ uint32_t block_excl_scan_smem(T* a, int m, uint32_t* 
   return total;
 }
 
+// Lanes of the warp whose digit (BITS bits) equals this lane's, among the
+// lanes with valid set; an invalid lane gets only itself.  One ballot per
+// digit bit (measured faster on GB300 than the hardware match instruction,
+// which HG_MATCH_BALLOT=0 selects).
+#ifndef HG_MATCH_BALLOT
+#define HG_MATCH_BALLOT 1
+#endif
+template <int BITS>
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d, bool valid) {
+#if HG_MATCH_BALLOT
+  uint32_t m = __ballot_sync(kFull, valid);
+#pragma unroll
+  for (int b = 0; b < BITS; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const uint32_t v = __ballot_sync(kFull, bit);
+    m &= bit ? v : ~v;
+  }
+  return valid ? m : (1u << (threadIdx.x & 31u));
+#else
+  return __match_any_sync(kFull, valid ? d : (0x10000u + (threadIdx.x & 31u)));
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Stable block-wide ranking by a small digit (ndig <= 256).
 //
@@ -342,8 +365,8 @@ __device__ __forceinline__ void block_stable_rank(const uint32_t (&dig)[IPT], ui
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
     if (seg0 + (uint32_t)r * 32u < n) {  // warp-uniform
       const bool valid = idx < n;
-      const uint32_t d = valid ? dig[r] : (0x10000u + lane);
-      const uint32_t peers = __match_any_sync(kFull, d);
+      const uint32_t d = dig[r];
+      const uint32_t peers = warp_peers<8>(d, valid);
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
       if (valid && lane == leader) {

@@ -29,6 +29,8 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 struct DevInfo {
   int sms = 0;
   int max_smem_optin = 0;
+  int smem_per_sm = 0;    // shared memory of one SM (all resident CTAs together)
+  int smem_reserved = 0;  // shared memory the system reserves per CTA
 };
 const DevInfo& dev_info();
 

@@ -4,6 +4,10 @@
 
 #include "hg_device.cuh"
 
+#ifndef HG_RANK_ATOMIC
+#define HG_RANK_ATOMIC 0
+#endif
+
 namespace hg {
 
 // Shared-memory words of block_stable_rank's counter matrix for 256 digits.
@@ -57,17 +61,20 @@ __device__ __forceinline__ void tile_partition_out(const K (&key)[IPT], const ui
 // while the cursors advance in the same step, and the counter matrix is
 // cleared after its last read, so it is already zero for the next tile.
 // Preconditions: wc[0 .. 256*rank_row<NW>()) is zero; ndig <= blockDim.x.
-template <typename K, int IPT, int NW>
+// IMPLICIT: val[r] is the element's index in the tile (< 2^16) and its id is
+// id_base + val[r]; the index and the digit then share one shared-memory
+// word (sd is unused).
+template <typename K, int IPT, int NW, bool IMPLICIT>
 __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const uint32_t (&val)[IPT],
                                                     const uint32_t (&dig)[IPT], uint32_t n, int ndig, K* sk,
                                                     uint32_t* sv, uint8_t* sd, uint32_t* wc, uint32_t* delta,
                                                     uint32_t* cursor, uint32_t* wsum, K* __restrict__ out_k,
-                                                    uint32_t* __restrict__ out_v) {
+                                                    uint32_t* __restrict__ out_v, uint32_t id_base) {
   constexpr int S = rank_row<NW>();
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t seg0 = (uint32_t)w * (32u * IPT);
   const uint32_t lt = lanemask_lt();
-  // Ranks inside each round come from __match_any_sync; the round's leader
+  // Ranks inside each round come from warp_peers; the round's leader
   // carries the warp's running count of the digit (plain shared-memory
   // read-modify-write, ordered from round to round by __syncwarp).
   uint32_t rank[IPT];
@@ -77,14 +84,18 @@ __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const u
     rank[r] = 0;
     if (seg0 + (uint32_t)r * 32u < n) {  // warp-uniform
       const bool valid = idx < n;
-      const uint32_t d = valid ? dig[r] : (0x10000u + lane);
-      const uint32_t peers = __match_any_sync(kFull, d);
+      const uint32_t d = dig[r];
+      const uint32_t peers = warp_peers<8>(d, valid);
       const int leader = __ffs(peers) - 1;
       uint32_t old = 0;
+#if HG_RANK_ATOMIC
+      if (valid && lane == leader) old = atomicAdd(&wc[d * S + w], (uint32_t)__popc(peers));
+#else
       if (valid && lane == leader) {
         old = wc[d * S + w];
         wc[d * S + w] = old + __popc(peers);
       }
+#endif
       old = __shfl_sync(kFull, old, leader);
       rank[r] = old + __popc(peers & lt);
       __syncwarp();
@@ -117,15 +128,26 @@ __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const u
       const uint32_t d = dig[r];
       const uint32_t dest = wc[d * S + NW] + wc[d * S + w] + rank[r];
       sk[dest] = key[r];
-      sv[dest] = val[r];
-      sd[dest] = (uint8_t)d;
+      if (IMPLICIT) {
+        sv[dest] = val[r] | (d << 16);
+      } else {
+        sv[dest] = val[r];
+        sd[dest] = (uint8_t)d;
+      }
     }
   }
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
-    const uint32_t g = delta[sd[j]] + j;
-    out_k[g] = sk[j];
-    out_v[g] = sv[j];
+    if (IMPLICIT) {
+      const uint32_t x = sv[j];
+      const uint32_t g = delta[x >> 16] + j;
+      out_k[g] = sk[j];
+      out_v[g] = id_base + (x & 0xffffu);
+    } else {
+      const uint32_t g = delta[sd[j]] + j;
+      out_k[g] = sk[j];
+      out_v[g] = sv[j];
+    }
   }
   for (int i = threadIdx.x; i < ndig * S; i += blockDim.x) wc[i] = 0;
   __syncthreads();
