@@ -126,10 +126,15 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
  * buffers of n keys, table->n must equal n) with implicit ids, the queries
  * are probed (binned when d_probe_ws is given, else direct) into d_counts
  * [q], and the counts are copied back to h_counts [q].  Everything is
- * asynchronous on `stream` (host buffers should be pinned for the copies to
- * overlap other work); h_counts is valid after the stream is synchronised.
- * Workspaces as for hg_build and hg_probe_binned.  No counterpart in the
- * paper: it is the whole hot path behind one call. */
+ * asynchronous with respect to the host (host buffers should be pinned for
+ * the copies to overlap other work); h_counts is valid after `stream` is
+ * synchronised.  The two host -> device copies run on a copy stream the
+ * library keeps per device, ordered after the work already queued on
+ * `stream` and joined back to `stream` by events, so the uploads of calls
+ * made on several streams (batches in flight) queue one after another and
+ * overlap the kernels of earlier calls instead of competing with each
+ * other.  Workspaces as for hg_build and hg_probe_binned.  No counterpart
+ * in the paper: it is the whole hot path behind one call. */
 hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t n, const void* h_queries,
                               uint64_t q, uint32_t* h_counts, void* d_keys, void* d_queries, uint32_t* d_counts,
                               const hg_table* table, void* d_build_ws, size_t build_ws_bytes, void* d_probe_ws,

@@ -173,6 +173,29 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
   });
 }
 
+// The upload stream of the current device (created on first use, kept until
+// exit): host -> device copies of hg_build_probe_host queue on it in call
+// order.
+static cudaStream_t upload_stream() {
+  static cudaStream_t streams[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
+// Records an event on `from` and makes `to` wait for it.
+static bool join(cudaStream_t from, cudaStream_t to) {
+  cudaEvent_t e;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+  const bool ok = cudaEventRecord(e, from) == cudaSuccess && cudaStreamWaitEvent(to, e, 0) == cudaSuccess;
+  cudaEventDestroy(e);  // released once it has completed
+  return ok;
+}
+
 hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t n, const void* h_queries,
                               uint64_t q, uint32_t* h_counts, void* d_keys, void* d_queries, uint32_t* d_counts,
                               const hg_table* table, void* d_build_ws, size_t build_ws_bytes, void* d_probe_ws,
@@ -183,13 +206,20 @@ hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t
     return HG_ERR_INVALID_ARG;
   const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
   cudaStream_t st = (cudaStream_t)stream;
-  if (n > 0 && cudaMemcpyAsync(d_keys, h_keys, n * kb, cudaMemcpyHostToDevice, st) != cudaSuccess) return HG_ERR_CUDA;
-  if (q > 0 && cudaMemcpyAsync(d_queries, h_queries, q * kb, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  cudaStream_t up = upload_stream();
+  if (!up) return HG_ERR_CUDA;
+  // uploads start once `stream` is done with the staging buffers, the build
+  // waits for the keys only, the probe for the queries as well
+  if (!join(st, up)) return HG_ERR_CUDA;
+  if (n > 0 && cudaMemcpyAsync(d_keys, h_keys, n * kb, cudaMemcpyHostToDevice, up) != cudaSuccess) return HG_ERR_CUDA;
+  if (!join(up, st)) return HG_ERR_CUDA;
+  if (q > 0 && cudaMemcpyAsync(d_queries, h_queries, q * kb, cudaMemcpyHostToDevice, up) != cudaSuccess)
     return HG_ERR_CUDA;
   // the table's buffers are this call's output (hg_table carries them as const for probes)
   rc = hg_build(cfg, d_keys, nullptr, n, const_cast<uint32_t*>(table->d_offsets), const_cast<void*>(table->d_keys),
                 const_cast<uint32_t*>(table->d_ids), d_build_ws, build_ws_bytes, stream);
   if (rc != HG_OK) return rc;
+  if (!join(up, st)) return HG_ERR_CUDA;
   if (q == 0) return HG_OK;
   rc = d_probe_ws ? hg_probe_binned(cfg, table, d_queries, q, d_counts, d_probe_ws, probe_ws_bytes, stream)
                   : hg_probe(cfg, table, d_queries, q, d_counts, stream);

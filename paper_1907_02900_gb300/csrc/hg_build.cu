@@ -469,22 +469,14 @@ struct recompute_bucket<MurmurMap> {
   static constexpr bool value = true;
 };
 
-// Warps that sort long buckets with position bitmaps: with a local-bucket
-// array its space holds sixteen bitmaps once it is dead; without one, four
-// bitmaps get their own space.
-template <bool LB>
-__host__ __device__ constexpr uint32_t bin_bitmap_warps() {
-  return LB ? kBinBitmapWarps : 4u;
-}
 
 // Shared memory of k_binbuild: staging buffers of keys and ids, the local
 // bucket array (LB), slot order (u16), packed u16 bucket counters, the list
-// of long buckets, the bitmaps (without LB) and small control state.
+// of long buckets, kBinBitmapWarps position bitmaps and small control state.
 size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
   size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + (lb ? (size_t)emax * 2 : 0) + (size_t)emax * 2 +
              (((size_t)1 << s) + 1) / 2 * 4 + ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2;
-  b = align_up(b, 16);
-  if (!lb) b += (size_t)bin_bitmap_warps<false>() * (emax / 32 + 1) * 4;
+  b = align_up(b, 16) + (size_t)kBinBitmapWarps * ((emax + 31) / 32) * 4;
   return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
 }
 
@@ -502,7 +494,7 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 // LB: the local buckets of step 1 are kept for step 3 (else recomputed).
 template <typename K, typename Map, int NWB, int MINB, bool LB>
 __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map map) {
-  constexpr uint32_t NBM = bin_bitmap_warps<LB>();
+  constexpr uint32_t NBM = kBinBitmapWarps;
   const uint32_t EB = a.emax + 16;
   const int nbuf = a.nbuf;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -515,9 +507,9 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   uint32_t* cnt = (uint32_t*)sp; sp += (((size_t)1 << a.s) + 1) / 2 * 4;
   uint16_t* heavy = (uint16_t*)sp; sp += (size_t)(a.emax / (kBinSmallBucket + 1) + 2) * 2;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
-  const uint32_t bm_words = (a.emax + 31) / 32;  // emax is a multiple of 32 when LB
-  uint32_t* bitmaps = LB ? (uint32_t*)lb : (uint32_t*)sp;  // NBM bitmaps of bm_words words
-  if (!LB) sp += (size_t)NBM * bm_words * 4;
+  const uint32_t bm_words = (a.emax + 31) / 32;
+  uint32_t* bitmaps = (uint32_t*)sp;  // NBM bitmaps of bm_words words
+  sp += (size_t)NBM * bm_words * 4;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
   uint32_t* nheavy = (uint32_t*)sp; sp += 16;
@@ -589,10 +581,11 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       atomicAdd(&cnt[l >> 1], 1u << ((l & 1u) << 4));
     }
     __syncthreads();
-    // 2. exclusive scan of the counts; every thread keeps its word range
-    const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
-    const uint32_t w0 = min(threadIdx.x * per, nwords), w1 = min(w0 + per, nwords);
+    // 2. exclusive scan of the counts; buckets above kBinSmallBucket edges
+    //    are listed for the bitmap sort
     {
+      const uint32_t per = (nwords + blockDim.x - 1) / blockDim.x;
+      const uint32_t w0 = min(threadIdx.x * per, nwords), w1 = min(w0 + per, nwords);
       uint32_t sum = 0;
       for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t x = cnt[w];
@@ -600,9 +593,11 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       }
       uint32_t base = block_excl_scan_nt<uint32_t>(sum, wsum);
       for (uint32_t w = w0; w < w1; ++w) {
-        const uint32_t x = cnt[w], lo = x & 0xffffu;
+        const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
+        if (lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
+        if (hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
         cnt[w] = base | ((base + lo) << 16);
-        base += lo + (x >> 16);
+        base += lo + hi;
       }
     }
     __syncthreads();
@@ -614,35 +609,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       opos[(old >> sh) & 0xffffu] = (uint16_t)e;
     }
     __syncthreads();
-    // 4. order inside each bucket of two or more edges (every counter now
-    //    holds its bucket's end): this thread's buckets 2*w0 .. 2*w1-1
-    {
-      uint32_t prev = w0 ? cnt[w0 - 1] >> 16 : 0u;  // end of bucket 2*w0 - 1
-      for (uint32_t w = w0; w < w1; ++w) {
-        const uint32_t x = cnt[w];
-        const uint32_t ends[2] = {x & 0xffffu, x >> 16};
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint32_t beg = prev, end = ends[h];
-          prev = end;
-          if (end - beg < 2) continue;
-          if (end - beg <= kBinSmallBucket) {
-            for (uint32_t k = beg + 1; k < end; ++k) {
-              const uint16_t p = opos[k];
-              uint32_t j = k;
-              while (j > beg && opos[j - 1] > p) {
-                opos[j] = opos[j - 1];
-                --j;
-              }
-              opos[j] = p;
-            }
-          } else {
-            heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + h);
-          }
-        }
-      }
-    }
-    __syncthreads();
+    // 4. long buckets (every counter now holds its bucket's end): slots
+    //    sorted by position with per-warp position bitmaps
     const uint32_t nh = *nheavy;
     if (nh > 0 && warp < NBM) {
       // each of the first NBM warps owns one bitmap of E bits
@@ -676,12 +644,26 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       }
     }
     if (nh > 0) __syncthreads();  // block-uniform: every thread read the same count
-    // 5. edges in bucket order; the bin's offsets (bucket v starts where
-    //    bucket v - 1 ends)
+    // 5. edges in canonical order: the edge in slot j of a bucket of at most
+    //    kBinSmallBucket edges goes to the bucket's start plus the number of
+    //    its edges with a smaller position (positions are distinct, so the
+    //    ranks are a permutation of the bucket's slots; the stores of a warp
+    //    stay within a few sectors); a long bucket is already in order.
+    //    Then the bin's offsets (bucket v starts where bucket v - 1 ends).
     for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
       const uint32_t p = opos[j];
-      a.csr_k[start + j] = kk[p];
-      a.csr_i[start + j] = map.out_id(ii[p]);
+      const K key = kk[p];
+      const uint32_t id = ii[p];
+      const uint32_t l = LB ? (uint32_t)lb[p] : map(key, id) - (uint32_t)bucket0;
+      const uint32_t end = (cnt[l >> 1] >> ((l & 1u) << 4)) & 0xffffu;
+      const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
+      uint32_t dst = j;
+      if (end - beg > 1 && end - beg <= kBinSmallBucket) {
+        dst = beg;
+        for (uint32_t i = beg; i < end; ++i) dst += opos[i] < p;
+      }
+      a.csr_k[start + dst] = key;
+      a.csr_i[start + dst] = map.out_id(id);
     }
     for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
       const uint32_t first = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
@@ -714,7 +696,6 @@ static BinCfg bin_config(const Plan& p, bool recompute) {
     const double mean = p.nbins ? (double)p.n / (double)p.nbins : 0.0;
     const size_t sm_cap = (size_t)di.smem_per_sm / 2 - (size_t)di.smem_reserved;
     uint32_t e = p.emax;
-    // (multiples of 32, so that the sixteen bitmaps fit in the local-bucket array)
     while (e > 1024 && (bin_smem_bytes(p.kb, e, p.s, 1, lb) > sm_cap ||
                         bin_smem_bytes(p.kb, e, p.s, 1, lb) > (size_t)di.max_smem_optin))
       e -= 32;
@@ -1394,6 +1375,9 @@ __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t*
   }
 }
 
+#ifndef HG_PROBE_GROUP_BITS
+#define HG_PROBE_GROUP_BITS 7  // log2 of the query groups (at most 8; 7 measured best at 2^28)
+#endif
 bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePlan* p) {
   const DevInfo& di = dev_info();
   const int kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
@@ -1403,7 +1387,7 @@ bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePl
   // with many groups every output tile of the merge draws on many of them,
   // which keeps its warps evenly loaded.
   (void)table_n;
-  int sg = ceil_log2_u64(V) - 8;
+  int sg = ceil_log2_u64(V) - HG_PROBE_GROUP_BITS;
   if (sg < 0) sg = 0;
   p->sg = (uint32_t)sg;
   p->ng = (uint32_t)(((V - 1) >> sg) + 1);

@@ -4,9 +4,6 @@
 
 #include "hg_device.cuh"
 
-#ifndef HG_RANK_ATOMIC
-#define HG_RANK_ATOMIC 0
-#endif
 
 namespace hg {
 
@@ -60,7 +57,8 @@ __device__ __forceinline__ void tile_partition_out(const K (&key)[IPT], const ui
 // per-digit output bases are computed once as delta[d] = cursor[d] - start[d]
 // while the cursors advance in the same step, and the counter matrix is
 // cleared after its last read, so it is already zero for the next tile.
-// Preconditions: wc[0 .. 256*rank_row<NW>()) is zero; ndig <= blockDim.x.
+// Preconditions: wc[0 .. 256*rank_row<NW>()) is zero and 16-byte aligned;
+// ndig <= blockDim.x.
 // IMPLICIT: val[r] is the element's index in the tile (< 2^16) and its id is
 // id_base + val[r]; the index and the digit then share one shared-memory
 // word (sd is unused).
@@ -74,29 +72,24 @@ __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const u
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t seg0 = (uint32_t)w * (32u * IPT);
   const uint32_t lt = lanemask_lt();
-  // Ranks inside each round come from warp_peers; the round's leader
-  // carries the warp's running count of the digit (plain shared-memory
-  // read-modify-write, ordered from round to round by __syncwarp).
+  // Ranks inside each round come from warp_peers (computed for all rounds
+  // first: they are independent); then, round by round, every lane reads
+  // its digit's warp counter and the round's leader (lowest lane of its
+  // peer group) stores the advanced count, ordered by __syncwarp.
   uint32_t rank[IPT];
 #pragma unroll
   for (int r = 0; r < IPT; ++r) {
     const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
-    rank[r] = 0;
+    rank[r] = seg0 + (uint32_t)r * 32u < n ? warp_peers<8>(dig[r], idx < n) : 0u;  // warp-uniform test
+  }
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
     if (seg0 + (uint32_t)r * 32u < n) {  // warp-uniform
-      const bool valid = idx < n;
-      const uint32_t d = dig[r];
-      const uint32_t peers = warp_peers<8>(d, valid);
-      const int leader = __ffs(peers) - 1;
-      uint32_t old = 0;
-#if HG_RANK_ATOMIC
-      if (valid && lane == leader) old = atomicAdd(&wc[d * S + w], (uint32_t)__popc(peers));
-#else
-      if (valid && lane == leader) {
-        old = wc[d * S + w];
-        wc[d * S + w] = old + __popc(peers);
-      }
-#endif
-      old = __shfl_sync(kFull, old, leader);
+      const bool valid = seg0 + (uint32_t)r * 32u + lane < n;
+      const uint32_t d = dig[r], peers = rank[r];
+      const uint32_t old = wc[d * S + w];
+      __syncwarp();
+      if (valid && (peers & lt) == 0u) wc[d * S + w] = old + __popc(peers);
       rank[r] = old + __popc(peers & lt);
       __syncwarp();
     }
@@ -149,7 +142,9 @@ __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const u
       out_v[g] = sv[j];
     }
   }
-  for (int i = threadIdx.x; i < ndig * S; i += blockDim.x) wc[i] = 0;
+  // (16-byte stores; 256 * S words are allocated, a multiple of four)
+  for (int i = threadIdx.x; i < (ndig * S + 3) / 4; i += blockDim.x)
+    reinterpret_cast<uint4*>(wc)[i] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
 }
 

@@ -215,3 +215,44 @@ def test_build_probe_host_buffers(hg, orc, pinned, binned):
     off, ck, ci = table_np(t)
     roff, rk, ri = orc.build(keys, V)
     assert np.array_equal(off, roff) and np.array_equal(ck, rk) and np.array_equal(ci, ri)
+
+
+def test_build_probe_host_batches_in_flight(hg, orc):
+    """Several host-buffer calls on two streams that reuse two sets of device
+    staging buffers: every call's counts and last table equal the oracle's
+    (the uploads, which queue on the library's copy stream, must wait for the
+    earlier call that used the same buffers)."""
+    import torch
+    n, V, calls = (1 << 17) + 5, 1 << 17, 6
+    cfg = hg.make_config(hg.KEY_U32, V, 0, "v2")
+    dev = "cuda"
+    hosts = []
+    for i in range(calls):
+        keys = dg.uniform_keys_u32(n, 300 + i)
+        q = dg.queries_u32(n, keys, 0.5, 400 + i)
+        hosts.append((keys, q, torch.from_numpy(keys.view(np.int32).copy()).pin_memory(),
+                      torch.from_numpy(q.view(np.int32).copy()).pin_memory(),
+                      torch.zeros(n, dtype=torch.int32).pin_memory()))
+    slots = []
+    for _ in range(2):
+        t = hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=dev), torch.empty(n, dtype=torch.uint32, device=dev),
+                     torch.empty(n, dtype=torch.uint32, device=dev), cfg)
+        slots.append({"stream": torch.cuda.Stream(), "t": t,
+                      "ws": torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=dev),
+                      "pws": torch.empty(hg.probe_workspace_size(t, n), dtype=torch.uint8, device=dev),
+                      "dk": torch.empty(n, dtype=torch.uint32, device=dev),
+                      "dq": torch.empty(n, dtype=torch.uint32, device=dev),
+                      "dc": torch.empty(n, dtype=torch.uint32, device=dev)})
+    for i in range(calls):
+        sl = slots[i % 2]
+        _, _, hk, hq, hc = hosts[i]
+        hg.build_probe_host(cfg, hk, hq, hc, sl["dk"], sl["dq"], sl["dc"], sl["t"], sl["ws"], sl["pws"],
+                            stream=sl["stream"])
+    torch.cuda.synchronize()
+    for i in range(calls):
+        keys, q, _, _, hc = hosts[i]
+        assert np.array_equal(hc.numpy().view(np.uint32), orc.multiplicity(keys, q)), i
+    for i in (calls - 2, calls - 1):
+        off, ck, ci = table_np(slots[i % 2]["t"])
+        roff, rk, ri = orc.build(hosts[i][0], V)
+        assert np.array_equal(off, roff) and np.array_equal(ck, rk) and np.array_equal(ci, ri), i
