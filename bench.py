@@ -46,6 +46,7 @@ UNIT = "Gkeys/s"
 WORKLOADS = ("scale", "plain", "join", "batched", "learned")
 
 
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -57,6 +58,7 @@ def parse():
     ap.add_argument("--log2v", type=int, default=None)
     ap.add_argument("--hit", type=float, default=0.5)
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-slots", type=int, default=2, help="batches in flight in the end-to-end measurement")
     ap.add_argument("--standard-probe", action="store_true", help="time HashGraph-Probe-Standard instead of the binned probe")
     ap.add_argument("--algo", choices=["v2", "v1"], default="v2", help="build algorithm (Alg. 2 or Alg. 1)")
     ap.add_argument("--explicit-ids", action="store_true", help="build with a uint32 id array (+4 B read per key)")
@@ -422,11 +424,12 @@ def run_scale(c: Ctx):
     if args.e2e_steps > 0:
         # Through the public host-buffer call (hg_build_probe_host): keys and
         # queries from pinned host memory, counts back to pinned host memory,
-        # every step.  Two batches in flight on two streams, as a serving loop
-        # would run it, so one batch's copies overlap the other's kernels.
+        # every step.  Several batches in flight on their own streams, as a
+        # serving loop would run it, so one batch's copies overlap the others'
+        # kernels.
         del ws, offsets, ck, ci, counts, pws, table
         slots = []
-        for _ in range(2):
+        for _ in range(args.e2e_slots):
             sl = {"stream": torch.cuda.Stream(device=c.dev),
                   "dk": torch.empty(n, dtype=torch.uint32, device=c.dev),
                   "dq": torch.empty(q, dtype=torch.uint32, device=c.dev),
@@ -441,11 +444,11 @@ def run_scale(c: Ctx):
             slots.append(sl)
 
         def host_step(i):
-            sl = slots[i % 2]
+            sl = slots[i % args.e2e_slots]
             hg.build_probe_host(cfg, keys_p, q_p, sl["hc"], sl["dk"], sl["dq"], sl["dc"], sl["table"], sl["ws"],
                                 sl["pws"], stream=sl["stream"])
 
-        for i in range(2):   # warm-up of both slots
+        for i in range(args.e2e_slots):   # warm-up of every slot
             host_step(i)
         torch.cuda.synchronize()
         c.barrier()
@@ -462,11 +465,12 @@ def run_scale(c: Ctx):
         torch.cuda.synchronize()
         c.barrier()
         e2e_value, _ = c.rate((n + q) * args.e2e_steps, e0.elapsed_time(e1))
-        ok = bool(np.array_equal(slots[(args.e2e_steps - 1) % 2]["hc"].numpy().view(np.uint32),
-                                 slots[(args.e2e_steps - 1) % 2]["dc"].cpu().numpy()))
+        last = slots[(args.e2e_steps - 1) % args.e2e_slots]
+        ok = bool(np.array_equal(last["hc"].numpy().view(np.uint32), last["dc"].cpu().numpy()))
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * (n + q), "d2h_bytes_per_step": 4 * q,
-               "call": "hg_build_probe_host, pinned host buffers, 2 batches in flight", "counts_returned": ok}
+               "call": f"hg_build_probe_host, pinned host buffers, {args.e2e_slots} batches in flight",
+               "counts_returned": ok}
         del slots
 
     cpu = None

@@ -1118,8 +1118,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.BS = BS;
   pa.status = status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, kPartIPT, false, kPartNW);
-    auto kern = k_partition<K, Map, false, kPartIPT, kPartNW, kPartMinBlocks>;
+    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt<K>(), false, kPartNW);
+    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks>;
     set_smem_once(kern, sm);
     {
       HG_TRACE("k_partition_A", st);
@@ -1458,8 +1458,8 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.BS = GS;
   pa.status = &hdr->status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), false, kPartIPT, false, kPartNW);
-    auto kern = k_partition<K, Map, false, kPartIPT, kPartNW, kPartMinBlocks>;
+    const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt<K>(), false, kPartNW);
+    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks>;
     set_smem_once(kern, sm);
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
@@ -1543,8 +1543,8 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
   uint32_t* ids = (uint32_t*)(ws + o[6]);
   uint64_t* src = keys;
   uint64_t* dst = tmp;
-  const size_t psm = part_smem_bytes(8, false, kPartIPT, false, kPartNW);
-  auto kp = k_partition<uint64_t, RadixByteMap, false, kPartIPT, kPartNW, kPartMinBlocks>;
+  const size_t psm = part_smem_bytes(8, false, part_ipt<uint64_t>(), false, kPartNW);
+  auto kp = k_partition<uint64_t, RadixByteMap, false, part_ipt<uint64_t>(), kPartNW, kPartMinBlocks>;
   set_smem_once(kp, psm);
   auto kh = k_hist<uint64_t, RadixByteMap>;
   set_smem_once(kh, 1024);

@@ -28,7 +28,16 @@ constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local ind
 #define HG_PARTB_MINB 4
 #endif
 constexpr int kPartNW = HG_PART_NW;      // warps of the partition kernels (pass A, query grouping)
-constexpr int kPartIPT = HG_PART_IPT;    // items per thread, pass A
+#ifndef HG_PART_IPT64
+#define HG_PART_IPT64 4
+#endif
+constexpr int kPartIPT = HG_PART_IPT;    // items per thread, pass A (4-byte keys)
+// pass A items per thread for K: 8-byte keys take a smaller tile, so that
+// two CTAs fit in one SM's shared memory
+template <typename K>
+constexpr int part_ipt() {
+  return sizeof(K) == 8 ? HG_PART_IPT64 : HG_PART_IPT;
+}
 constexpr int kPartIPTB = HG_PART_IPTB;  // items per thread, pass B
 constexpr int kPartMinBlocks = HG_PART_MINB;
 constexpr int kPartBNW = HG_PARTB_NW;    // pass B: smaller CTAs, more of them per SM
