@@ -119,15 +119,23 @@ __device__ __forceinline__ void unpack16<uint64_t>(const uint4& x, uint64_t (&k)
   k[1] = ((uint64_t)x.w << 32) | x.z;
 }
 
+// Shared memory of k_hist: the histogram (at least 1 KB), then the bucket
+// map's staged tables (Map::kStageBytes).
+__host__ __device__ inline size_t hist_stage_offset(uint32_t nbins) {
+  return align_up((size_t)(nbins < 256u ? 256u : nbins) * 4, 16);
+}
+
 // Phase 1: per-chunk bin histogram in shared memory; per super-bin sums.
 template <typename K, typename Map>
 __global__ void __launch_bounds__(kHistThreads) k_hist(const K* __restrict__ keys, uint64_t n,
                                                        uint64_t chunk, uint32_t s, uint32_t nbins,
                                                        uint32_t sshift, uint32_t nsb,
                                                        uint32_t* __restrict__ H,
-                                                       uint32_t* __restrict__ C, Map map) {
-  extern __shared__ uint32_t hist[];
+                                                       uint32_t* __restrict__ C, Map map,
+                                                       uint32_t stage_bytes) {
+  extern __shared__ __align__(16) uint32_t hist[];
   map.init();
+  map.stage((uint8_t*)hist + hist_stage_offset(nbins), stage_bytes);
   for (uint32_t i = threadIdx.x; i < nbins; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   constexpr int per = 16 / sizeof(K);
@@ -279,6 +287,7 @@ struct PartArgs {
   const uint32_t* CT;  // per super-bin totals
   const uint32_t* BS;  // bin starts
   uint32_t* status;
+  uint32_t stage_bytes;  // shared memory after the kernel's own, for the bucket map's tables
 };
 
 template <typename K, typename Map, bool PASS_B, int IPT, int NW, int MINB>
@@ -303,9 +312,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
   uint32_t* ilo = (uint32_t*)sp; sp += PASS_B ? kMaxItemsPerCta * 4 : 0;
   uint32_t* ihi = (uint32_t*)sp; sp += PASS_B ? kMaxItemsPerCta * 4 : 0;
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
-  uint64_t* bar = (uint64_t*)sp;
+  uint64_t* bar = (uint64_t*)sp; sp += 2 * 8;
+  uint8_t* stage = sp;  // a.stage_bytes (16-byte aligned)
 
   map.init();
+  map.stage(stage, a.stage_bytes);
   for (int i = threadIdx.x; i < rank_words<NW>(); i += blockDim.x) wc[i] = 0;
   const uint64_t nitems = PASS_B ? (uint64_t)a.nsb * a.ngroups : (uint64_t)a.G;
   if (PASS_B) {
@@ -1064,12 +1075,13 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   const DevInfo& di = dev_info();
 
   {
-    const size_t sm = (size_t)p.nbins * 4;
+    const size_t sm = hist_stage_offset(p.nbins) + Map::kStageBytes;
     auto kern = k_hist<K, Map>;
     set_smem_once(kern, sm);
     {
       HG_TRACE("k_hist", st);
-      kern<<<p.G, kHistThreads, sm, st>>>(keys, p.n, p.chunk, p.s, p.nbins, p.sshift, p.nsb, H, C, map);
+      kern<<<p.G, kHistThreads, sm, st>>>(keys, p.n, p.chunk, p.s, p.nbins, p.sshift, p.nsb, H, C, map,
+                                          (uint32_t)Map::kStageBytes);
     }
   }
   {
@@ -1118,7 +1130,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.BS = BS;
   pa.status = status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt<K>(), false, kPartNW);
+    pa.stage_bytes = (uint32_t)Map::kStageBytes;
+    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt<K>(), false, kPartNW) + pa.stage_bytes;
     auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks>;
     set_smem_once(kern, sm);
     {
@@ -1132,6 +1145,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     pb.in_i = csr_i;
     pb.out_k = bk;
     pb.out_i = bi;
+    pb.stage_bytes = 0;  // (staging would cost pass B a resident CTA per SM)
     const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true, kPartBNW);
     auto kern = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks>;
     set_smem_once(kern, sm);
@@ -1424,11 +1438,12 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   uint32_t* qc = (uint32_t*)(ws + p.o_qc);
   const DevInfo& di = dev_info();
   {
-    const size_t sm = (size_t)p.ng * 4;
+    const size_t sm = hist_stage_offset(p.ng) + Map::kStageBytes;
     auto kern = k_hist<K, Map>;
-    set_smem_once(kern, std::max<size_t>(sm, 1024));
+    set_smem_once(kern, sm);
     HG_TRACE("k_hist_Q", st);
-    kern<<<p.G, kHistThreads, std::max<size_t>(sm, 1024), st>>>(queries, q, p.chunk, p.sg, p.ng, 0, p.ng, H, C, map);
+    kern<<<p.G, kHistThreads, sm, st>>>(queries, q, p.chunk, p.sg, p.ng, 0, p.ng, H, C, map,
+                                        (uint32_t)Map::kStageBytes);
   }
   {
     HG_TRACE("k_colscan_Q", st);
@@ -1458,7 +1473,8 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.BS = GS;
   pa.status = &hdr->status;
   {
-    const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt<K>(), false, kPartNW);
+    pa.stage_bytes = (uint32_t)Map::kStageBytes;
+    const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt<K>(), false, kPartNW) + pa.stage_bytes;
     auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks>;
     set_smem_once(kern, sm);
     HG_TRACE("k_partition_Q", st);
@@ -1493,8 +1509,10 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
 // ===========================================================================
 struct RadixByteMap {
   static constexpr bool kNeedsPos = false;
+  static constexpr size_t kStageBytes = 0;
   uint32_t shift;
   __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void stage(uint8_t*, size_t) {}
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
     return (uint32_t)(((uint64_t)key >> shift) & 255u);
@@ -1547,12 +1565,13 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
   auto kp = k_partition<uint64_t, RadixByteMap, false, part_ipt<uint64_t>(), kPartNW, kPartMinBlocks>;
   set_smem_once(kp, psm);
   auto kh = k_hist<uint64_t, RadixByteMap>;
-  set_smem_once(kh, 1024);
+  const size_t hsm = hist_stage_offset(256);
+  set_smem_once(kh, hsm);
   for (uint32_t pass = 0; pass < 8; ++pass) {
     RadixByteMap map{8 * pass};
     {
       HG_TRACE("k_radix_hist", st);
-      kh<<<G, kHistThreads, 1024, st>>>(src, n, chunk, 0, 256, 0, 256, H, C, map);
+      kh<<<G, kHistThreads, hsm, st>>>(src, n, chunk, 0, 256, 0, 256, H, C, map, 0u);
     }
     {
       HG_TRACE("k_radix_scan", st);

@@ -67,9 +67,11 @@ struct FastMod {
 // Eq. 1: bucket = hash(key) mod V.
 struct MurmurMap {
   static constexpr bool kNeedsPos = false;
+  static constexpr size_t kStageBytes = 0;  // shared memory stage() can use
   uint32_t seed;
   FastMod mod;
   __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void stage(uint8_t*, size_t) {}
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
     return mod(murmur3(key, seed));
@@ -91,6 +93,7 @@ struct MurmurMap {
 // the buckets bucket_base + [0, V).
 struct BatchedMap {
   static constexpr bool kNeedsPos = true;
+  static constexpr size_t kStageBytes = 0;
   uint32_t seed;
   uint32_t page_shift;
   uint64_t pos_base;
@@ -100,6 +103,7 @@ struct BatchedMap {
   const uint32_t* page;   // table holding position (p << page_shift)
   const uint4* desc;      // per table: {global bucket base, V_t, fastmod M low, M high}
   __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void stage(uint8_t*, size_t) {}
   __device__ __forceinline__ uint32_t table_of(uint64_t p) const {
     uint32_t t = __ldg(page + (p >> page_shift));
     while (__ldg((const unsigned long long*)begin + t + 1) <= p) ++t;
@@ -151,14 +155,18 @@ __device__ __forceinline__ float rmi_feature(uint64_t key) {
   return __uint2float_rn(__float_as_uint(__ull2float_rn(key)));
 }
 
+constexpr uint32_t kStageLeaves = 1024;  // leaf records a kernel can stage in shared memory
+
 struct LearnedMap {
   static constexpr bool kNeedsPos = false;
+  static constexpr size_t kStageBytes = kStageLeaves * sizeof(LearnedLeaf);
   const uint8_t* blob;  // device pointer
   uint64_t Vcap;        // buckets of the table being built (host-provided bound)
   float a, b, Lf;
   uint32_t L;
   uint64_t V, vmax;
   const LearnedLeaf* leaves;
+  uint32_t sleaves;     // shared-memory address of the staged leaves (0: not staged)
   __device__ __forceinline__ void init() {
     L = __ldg((const uint32_t*)(blob + 4));
     V = __ldg((const unsigned long long*)(blob + 8));
@@ -167,6 +175,19 @@ struct LearnedMap {
     Lf = __uint2float_rn(L);
     vmax = V < Vcap ? V : Vcap;
     leaves = (const LearnedLeaf*)(blob + kModelHeaderBytes);
+    sleaves = 0;
+  }
+  // Copies the leaf records into `smem` (16-byte aligned, `bytes` long)
+  // when they fit, so that inference reads them from shared memory.  Every
+  // thread of the block must call it (after init()); it ends with a barrier.
+  __device__ __forceinline__ void stage(uint8_t* smem, size_t bytes) {
+    if ((size_t)L * sizeof(LearnedLeaf) <= bytes) {
+      const unsigned long long* src = (const unsigned long long*)leaves;
+      unsigned long long* dst = (unsigned long long*)smem;
+      for (uint32_t i = threadIdx.x; i < L * 3; i += blockDim.x) dst[i] = __ldg(src + i);
+      sleaves = (uint32_t)__cvta_generic_to_shared(smem);
+    }
+    __syncthreads();
   }
   template <typename K>
   __device__ __forceinline__ uint32_t leaf_of(K key) const {
@@ -178,12 +199,23 @@ struct LearnedMap {
   __device__ __forceinline__ uint32_t out_id(uint32_t id) const { return id; }
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
-    // a leaf record is 24 bytes at an 8-byte boundary: three 8-byte loads
-    const unsigned long long* rec = (const unsigned long long*)(leaves + leaf_of(key));
-    const uint64_t xmin = __ldg(rec);
-    const float2 si = __ldg((const float2*)(rec + 1));
-    const uint2 bw = __ldg((const uint2*)(rec + 2));
-    const float slope = si.x, icpt = si.y;
+    // a leaf record is 24 bytes at an 8-byte boundary: three 8-byte loads,
+    // from shared memory when staged
+    const uint32_t j = leaf_of(key);
+    uint64_t xmin;
+    uint2 si, bw;
+    if (sleaves) {
+      const uint32_t a0 = sleaves + j * (uint32_t)sizeof(LearnedLeaf);
+      asm("ld.shared.u64 %0, [%1];" : "=l"(xmin) : "r"(a0));
+      asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(si.x), "=r"(si.y) : "r"(a0 + 8));
+      asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(bw.x), "=r"(bw.y) : "r"(a0 + 16));
+    } else {
+      const unsigned long long* rec = (const unsigned long long*)(leaves + j);
+      xmin = __ldg(rec);
+      si = __ldg((const uint2*)(rec + 1));
+      bw = __ldg((const uint2*)(rec + 2));
+    }
+    const float slope = __uint_as_float(si.x), icpt = __uint_as_float(si.y);
     const uint32_t base = bw.x, width = bw.y;
     uint32_t local = 0;
     if (width > 0) {
