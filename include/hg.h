@@ -130,11 +130,15 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
  * the copies to overlap other work); h_counts is valid after `stream` is
  * synchronised.  The two host -> device copies run on a copy stream the
  * library keeps per device, ordered after the work already queued on
- * `stream` and joined back to `stream` by events, so the uploads of calls
- * made on several streams (batches in flight) queue one after another and
- * overlap the kernels of earlier calls instead of competing with each
- * other.  Workspaces as for hg_build and hg_probe_binned.  No counterpart
- * in the paper: it is the whole hot path behind one call. */
+ * `stream` and joined back to `stream` by events, and the kernels of a call
+ * start after those of the previous call on the same device (on whatever
+ * stream).  Calls made on several streams (batches in flight) therefore
+ * queue their uploads one after another, run their kernels back to back,
+ * and overlap one call's copies with another's kernels.  Calls from several
+ * host threads are serialised while they enqueue.  Not meant for stream
+ * capture (the ordering events live outside any graph).  Workspaces as for
+ * hg_build and hg_probe_binned.  No counterpart in the paper: it is the
+ * whole hot path behind one call. */
 hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t n, const void* h_queries,
                               uint64_t q, uint32_t* h_counts, void* d_keys, void* d_queries, uint32_t* d_counts,
                               const hg_table* table, void* d_build_ws, size_t build_ws_bytes, void* d_probe_ws,

@@ -173,18 +173,24 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
   });
 }
 
-// The upload stream of the current device (created on first use, kept until
-// exit): host -> device copies of hg_build_probe_host queue on it in call
-// order.
-static cudaStream_t upload_stream() {
-  static cudaStream_t streams[64] = {};
-  static std::mutex mu;
+// Per-device state of hg_build_probe_host (created on first use, kept until
+// exit): the upload stream, on which the host -> device copies of all calls
+// queue in call order, and an event marking the end of the last call's
+// kernels, after which the next call's kernels start.
+struct HostPipe {
+  cudaStream_t up = nullptr;
+  cudaEvent_t done = nullptr;
+  bool recorded = false;
+};
+static std::mutex g_pipe_mu;
+static HostPipe* host_pipe() {
+  static HostPipe pipes[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
-    streams[dev] = nullptr;
-  return streams[dev];
+  HostPipe& p = pipes[dev];
+  if (!p.up && cudaStreamCreateWithFlags(&p.up, cudaStreamNonBlocking) != cudaSuccess) p.up = nullptr;
+  if (!p.done && cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming) != cudaSuccess) p.done = nullptr;
+  return p.up && p.done ? &p : nullptr;
 }
 
 // Records an event on `from` and makes `to` wait for it.
@@ -206,13 +212,19 @@ hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t
     return HG_ERR_INVALID_ARG;
   const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaStream_t up = upload_stream();
-  if (!up) return HG_ERR_CUDA;
+  // one call at a time per device enqueues, so that the device sees the
+  // calls in one order
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe* pp = host_pipe();
+  if (!pp) return HG_ERR_CUDA;
+  cudaStream_t up = pp->up;
   // uploads start once `stream` is done with the staging buffers, the build
-  // waits for the keys only, the probe for the queries as well
+  // waits for the keys and for the previous call's kernels, the probe for
+  // the queries as well
   if (!join(st, up)) return HG_ERR_CUDA;
   if (n > 0 && cudaMemcpyAsync(d_keys, h_keys, n * kb, cudaMemcpyHostToDevice, up) != cudaSuccess) return HG_ERR_CUDA;
   if (!join(up, st)) return HG_ERR_CUDA;
+  if (pp->recorded && cudaStreamWaitEvent(st, pp->done, 0) != cudaSuccess) return HG_ERR_CUDA;
   if (q > 0 && cudaMemcpyAsync(d_queries, h_queries, q * kb, cudaMemcpyHostToDevice, up) != cudaSuccess)
     return HG_ERR_CUDA;
   // the table's buffers are this call's output (hg_table carries them as const for probes)
@@ -224,6 +236,8 @@ hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t
   rc = d_probe_ws ? hg_probe_binned(cfg, table, d_queries, q, d_counts, d_probe_ws, probe_ws_bytes, stream)
                   : hg_probe(cfg, table, d_queries, q, d_counts, stream);
   if (rc != HG_OK) return rc;
+  if (cudaEventRecord(pp->done, st) != cudaSuccess) return HG_ERR_CUDA;
+  pp->recorded = true;
   if (cudaMemcpyAsync(h_counts, d_counts, q * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HG_ERR_CUDA;
   return HG_OK;
 }
