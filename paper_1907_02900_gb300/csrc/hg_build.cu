@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ ovf_list,
                                                     uint32_t* __restrict__ ovf_count,
                                                     uint32_t* __restrict__ offsets, uint64_t V,
-                                                    uint32_t n_end, HugeArgs h) {
+                                                    uint32_t n_end, HugeArgs h, uint32_t* order) {
   __shared__ uint32_t wsum[32];
   const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
   const uint32_t b = threadIdx.x * per, e = min(b + per, nbins);
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
     BS[i] = base;
     base += T[i];
     if (T[i] <= emax) continue;
+    if (order) *order = 1u;  // this bin is built outside shared memory: stable partitions needed
     if (h.list == nullptr || T[i] <= kHugeSeg) {
       ovf_list[atomicAdd(ovf_count, 1u)] = i;
       continue;
@@ -288,10 +289,18 @@ struct PartArgs {
   const uint32_t* BS;  // bin starts
   uint32_t* status;
   uint32_t stage_bytes;  // shared memory after the kernel's own, for the bucket map's tables
+  // order mode word (null: always stable); see k_partition
+  const uint32_t* order;
 };
 
-template <typename K, typename Map, bool PASS_B, int IPT, int NW, int MINB>
+// ANY: tiles ranked by shared-memory atomics, equal digits in any order
+// (tile_partition_any).  With a.order set, the build launches both variants
+// and the one that does not match the order mode written by k_scan_bins
+// returns at once: the unordered one runs only when every bin fits the
+// shared-memory bin build, which then restores the canonical order by id.
+template <typename K, typename Map, bool PASS_B, int IPT, int NW, int MINB, bool ANY>
 __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map map) {
+  if (a.order != nullptr && ((*(volatile const uint32_t*)a.order == 0u) != ANY)) return;
   constexpr uint32_t TILE = NW * 32 * IPT;
   constexpr uint32_t TB = TILE + 16;
   static_assert(TILE <= 65536, "tile indexes are packed into 16 bits");
@@ -439,12 +448,21 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
         dig[r] = 0;
       }
     }
-    if (has_ids)
-      tile_partition_fast<K, IPT, NW, false>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
-                                             a.out_k, a.out_i, 0u);
-    else
-      tile_partition_fast<K, IPT, NW, true>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
-                                            a.out_k, a.out_i, (uint32_t)cur.t0);
+    if (ANY) {
+      if (has_ids)
+        tile_partition_any<K, IPT, NW, false>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                              a.out_k, a.out_i, 0u);
+      else
+        tile_partition_any<K, IPT, NW, true>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                             a.out_k, a.out_i, (uint32_t)cur.t0);
+    } else {
+      if (has_ids)
+        tile_partition_fast<K, IPT, NW, false>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                               a.out_k, a.out_i, 0u);
+      else
+        tile_partition_fast<K, IPT, NW, true>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
+                                              a.out_k, a.out_i, (uint32_t)cur.t0);
+    }
     cur = nxt;
   }
 }
@@ -467,6 +485,7 @@ struct BinArgs {
   uint32_t pos_base;  // added to every offset written (position of element 0 in the CSR arrays)
   int nbuf;  // staging buffers: 2 = next bin prefetched during this one
   uint32_t* status;
+  const uint32_t* order;  // order mode word (null: partitions were stable); see k_partition
 };
 
 // Whether the bin build recomputes an edge's bucket rather than keeping it
@@ -503,8 +522,13 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 //   5. the edges are written out in slot order, and the bin's offsets
 //      (both coalesced)
 // LB: the local buckets of step 1 are kept for step 3 (else recomputed).
-template <typename K, typename Map, int NWB, int MINB, bool LB>
+// ANY: the partitions ranked tiles in any order (see k_partition), so the
+// bin positions no longer follow the input order; every bucket of two or
+// more edges is then ranked by id (an input position, distinct) instead,
+// whatever its length.
+template <typename K, typename Map, int NWB, int MINB, bool LB, bool ANY>
 __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map map) {
+  if (a.order != nullptr && ((*(volatile const uint32_t*)a.order == 0u) != ANY)) return;
   constexpr uint32_t NBM = kBinBitmapWarps;
   const uint32_t EB = a.emax + 16;
   const int nbuf = a.nbuf;
@@ -605,8 +629,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       uint32_t base = block_excl_scan_nt<uint32_t>(sum, wsum);
       for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
-        if (lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
-        if (hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
+        if (!ANY && lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
+        if (!ANY && hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
         cnt[w] = base | ((base + lo) << 16);
         base += lo + hi;
       }
@@ -659,7 +683,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     //    kBinSmallBucket edges goes to the bucket's start plus the number of
     //    its edges with a smaller position (positions are distinct, so the
     //    ranks are a permutation of the bucket's slots; the stores of a warp
-    //    stay within a few sectors); a long bucket is already in order.
+    //    stay within a few sectors); a long bucket is already in order.  With
+    //    ANY every bucket is ranked by id the same way.
     //    Then the bin's offsets (bucket v starts where bucket v - 1 ends).
     for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
       const uint32_t p = opos[j];
@@ -669,7 +694,12 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       const uint32_t end = (cnt[l >> 1] >> ((l & 1u) << 4)) & 0xffffu;
       const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
       uint32_t dst = j;
-      if (end - beg > 1 && end - beg <= kBinSmallBucket) {
+      if (ANY) {
+        if (end - beg > 1) {
+          dst = beg;
+          for (uint32_t i = beg; i < end; ++i) dst += ii[opos[i]] < id;
+        }
+      } else if (end - beg > 1 && end - beg <= kBinSmallBucket) {
         dst = beg;
         for (uint32_t i = beg; i < end; ++i) dst += opos[i] < p;
       }
@@ -1094,6 +1124,13 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   }
   const bool two = p.sshift > 0;
   const BinCfg bc = bin_config(p, recompute_bucket<Map>::value);
+  // Implicit ids are input positions, so the bin build can restore the
+  // canonical order (ascending position in every bucket) from the ids
+  // alone; then, unless k_scan_bins finds a bin too large for the
+  // shared-memory bin build, the partitions may rank tiles in any order.
+  // Both variants of each such kernel are launched; the one that does not
+  // match the order mode returns at once.
+  const bool any_order = ids == nullptr;
   {
     HG_TRACE("k_scan_bins", st);
     HugeArgs h{};
@@ -1106,7 +1143,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     h.max_rows = p.max_rows;
     h.status = status;
     k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, bc.emax, ovf, &hdr->ovf_count, offsets, p.V,
-                                    pos_base + (uint32_t)p.n, h);
+                                    pos_base + (uint32_t)p.n, h, any_order ? &hdr->order_mode : nullptr);
   }
 
   PartArgs<K> pa{};
@@ -1131,11 +1168,15 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.status = status;
   {
     pa.stage_bytes = (uint32_t)Map::kStageBytes;
+    pa.order = any_order ? &hdr->order_mode : nullptr;
     const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt<K>(), false, kPartNW) + pa.stage_bytes;
-    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks>;
+    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks, false>;
+    auto kany = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks, true>;
     set_smem_once(kern, sm);
+    set_smem_once(kany, sm);
     {
       HG_TRACE("k_partition_A", st);
+      if (any_order) kany<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
       kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
     }
   }
@@ -1147,8 +1188,10 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     pb.out_i = bi;
     pb.stage_bytes = 0;  // (staging would cost pass B a resident CTA per SM)
     const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true, kPartBNW);
-    auto kern = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks>;
+    auto kern = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks, false>;
+    auto kany = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks, true>;
     set_smem_once(kern, sm);
+    set_smem_once(kany, sm);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPartBNW * 32, sm);
     // ~32K edges per item: enough to amortise the per-item set-up
@@ -1160,6 +1203,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     grid = (unsigned)std::max<uint64_t>(grid, (items + kMaxItemsPerCta - 1) / kMaxItemsPerCta);
     {
       HG_TRACE("k_partition_B", st);
+      if (any_order) kany<<<grid, kPartBNW * 32, sm, st>>>(pb, map);
       kern<<<grid, kPartBNW * 32, sm, st>>>(pb, map);
     }
   }
@@ -1178,28 +1222,26 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   ba.pos_base = pos_base;
   ba.status = status;
   ba.nbuf = bc.nbuf;
+  ba.order = any_order ? &hdr->order_mode : nullptr;
   {
     unsigned grid = (unsigned)std::min<uint64_t>(p.nbins, (uint64_t)di.sms * bc.per_sm);
     grid = std::max<unsigned>(grid, (p.nbins + kMaxBinsPerCta - 1) / kMaxBinsPerCta);
     HG_TRACE("k_binbuild", st);
+    auto launch = [&](auto kern, auto kany, unsigned threads) {
+      set_smem_once(kern, bc.smem);
+      set_smem_once(kany, bc.smem);
+      if (any_order) kany<<<grid, threads, bc.smem, st>>>(ba, map);
+      kern<<<grid, threads, bc.smem, st>>>(ba, map);
+    };
     if (bc.per_sm == 2) {
-      if (bc.lb) {
-        auto kern = k_binbuild<K, Map, 16, 2, true>;
-        set_smem_once(kern, bc.smem);
-        kern<<<grid, 512, bc.smem, st>>>(ba, map);
-      } else {
-        auto kern = k_binbuild<K, Map, 16, 2, false>;
-        set_smem_once(kern, bc.smem);
-        kern<<<grid, 512, bc.smem, st>>>(ba, map);
-      }
+      if (bc.lb)
+        launch(k_binbuild<K, Map, 16, 2, true, false>, k_binbuild<K, Map, 16, 2, true, true>, 512);
+      else
+        launch(k_binbuild<K, Map, 16, 2, false, false>, k_binbuild<K, Map, 16, 2, false, true>, 512);
     } else if (bc.tpb == 512) {
-      auto kern = k_binbuild<K, Map, 16, 1, true>;
-      set_smem_once(kern, bc.smem);
-      kern<<<grid, 512, bc.smem, st>>>(ba, map);
+      launch(k_binbuild<K, Map, 16, 1, true, false>, k_binbuild<K, Map, 16, 1, true, true>, 512);
     } else {
-      auto kern = k_binbuild<K, Map, kBinNW, 1, true>;
-      set_smem_once(kern, bc.smem);
-      kern<<<grid, kBinNW * 32, bc.smem, st>>>(ba, map);
+      launch(k_binbuild<K, Map, kBinNW, 1, true, false>, k_binbuild<K, Map, kBinNW, 1, true, true>, kBinNW * 32);
     }
   }
   {
@@ -1453,7 +1495,7 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
     HG_TRACE("k_scan_Q", st);
     // no bin is "oversized" here; the closing-offset store goes to scratch
     k_scan_bins<<<1, 1024, 0, st>>>(CT, p.ng, GS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.ng, 0,
-                                    (uint32_t)q, HugeArgs{});
+                                    (uint32_t)q, HugeArgs{}, nullptr);
   }
   PartArgs<K> pa{};
   pa.in_k = queries;
@@ -1475,7 +1517,7 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   {
     pa.stage_bytes = (uint32_t)Map::kStageBytes;
     const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt<K>(), false, kPartNW) + pa.stage_bytes;
-    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks>;
+    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks, false>;
     set_smem_once(kern, sm);
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
@@ -1562,7 +1604,7 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
   uint64_t* src = keys;
   uint64_t* dst = tmp;
   const size_t psm = part_smem_bytes(8, false, part_ipt<uint64_t>(), false, kPartNW);
-  auto kp = k_partition<uint64_t, RadixByteMap, false, part_ipt<uint64_t>(), kPartNW, kPartMinBlocks>;
+  auto kp = k_partition<uint64_t, RadixByteMap, false, part_ipt<uint64_t>(), kPartNW, kPartMinBlocks, false>;
   set_smem_once(kp, psm);
   auto kh = k_hist<uint64_t, RadixByteMap>;
   const size_t hsm = hist_stage_offset(256);
@@ -1577,7 +1619,7 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
       HG_TRACE("k_radix_scan", st);
       k_colscan<<<1, 256, 0, st>>>(C, G, 256, CT);
       k_scan_bins<<<1, 1024, 0, st>>>(CT, 256, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + 256, 0, (uint32_t)n,
-                                      HugeArgs{});
+                                      HugeArgs{}, nullptr);
     }
     PartArgs<uint64_t> pa{};
     pa.in_k = src;

@@ -13,7 +13,8 @@ struct WsHeader {
   uint32_t status;      // hg_status recorded by device code (0 = OK)
   uint32_t ovf_count;   // number of oversized bins (build)
   uint32_t heavy_count; // number of heavy buckets (V1 fix-up, join)
-  uint32_t pad0;
+  uint32_t order_mode;  // V2 build with implicit ids: 0 = partitions may rank tiles in any
+                        // order (every bin fits shared memory), 1 = stable partitions needed
   uint64_t counters[8]; // scratch counters for kernels
   uint8_t reserved[256 - 16 - 64];
 };

@@ -148,6 +148,69 @@ __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const u
   __syncthreads();
 }
 
+// Partition of one tile in which equal digits need not keep their order:
+// every element takes its rank from a shared-memory atomic on its digit's
+// counter, so the tile costs one atomic per element and a 256-entry scan
+// instead of the ballots and per-warp counters of tile_partition_fast.
+// Used only where the bin build restores the canonical order by id.
+// Preconditions: tcnt[0 .. 256) is zero; ndig <= blockDim.x.  IMPLICIT as
+// for tile_partition_fast.
+template <typename K, int IPT, int NW, bool IMPLICIT>
+__device__ __forceinline__ void tile_partition_any(const K (&key)[IPT], const uint32_t (&val)[IPT],
+                                                   const uint32_t (&dig)[IPT], uint32_t n, int ndig, K* sk,
+                                                   uint32_t* sv, uint8_t* sd, uint32_t* tcnt, uint32_t* delta,
+                                                   uint32_t* cursor, uint32_t* wsum, K* __restrict__ out_k,
+                                                   uint32_t* __restrict__ out_v, uint32_t id_base) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const uint32_t seg0 = (uint32_t)w * (32u * IPT);
+  uint32_t rank[IPT];
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+    rank[r] = idx < n ? atomicAdd(&tcnt[dig[r]], 1u) : 0u;
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  const uint32_t tot = t < ndig ? tcnt[t] : 0u;
+  const uint32_t start = block_excl_scan_nt<uint32_t>(tot, wsum);
+  if (t < ndig) {
+    tcnt[t] = start;
+    delta[t] = cursor[t] - start;
+    cursor[t] += tot;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < IPT; ++r) {
+    const uint32_t idx = seg0 + (uint32_t)r * 32u + lane;
+    if (idx < n) {
+      const uint32_t d = dig[r];
+      const uint32_t dest = tcnt[d] + rank[r];
+      sk[dest] = key[r];
+      if (IMPLICIT) {
+        sv[dest] = val[r] | (d << 16);
+      } else {
+        sv[dest] = val[r];
+        sd[dest] = (uint8_t)d;
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+    if (IMPLICIT) {
+      const uint32_t x = sv[j];
+      const uint32_t g = delta[x >> 16] + j;
+      out_k[g] = sk[j];
+      out_v[g] = id_base + (x & 0xffffu);
+    } else {
+      const uint32_t g = delta[sd[j]] + j;
+      out_k[g] = sk[j];
+      out_v[g] = sv[j];
+    }
+  }
+  for (int i = t; i < 256; i += blockDim.x) tcnt[i] = 0;
+  __syncthreads();
+}
+
 // Stable counting sort of tile positions 0..n-1 by a local bucket index
 // lb[p] < nb (nb <= 65536), by two least-significant-digit passes that split
 // the index bits evenly (one pass when nb <= 256).  Returns the array
