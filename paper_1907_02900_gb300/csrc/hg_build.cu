@@ -1016,7 +1016,7 @@ __global__ void __launch_bounds__(kV1HeavyNW * 32) k_v1_fix_heavy(const uint32_t
                                                                  const uint32_t* heavy_count, K* csr_k,
                                                                  uint32_t* csr_i, K* tmp_k, uint32_t* tmp_i,
                                                                  uint32_t nbits) {
-  constexpr int NW = kV1HeavyNW, IPT = kPartIPT;
+  constexpr int NW = kV1HeavyNW, IPT = kV1HeavyIPT;
   constexpr uint32_t TILE = NW * 32 * IPT;
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* sp = smem;
@@ -1169,9 +1169,9 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   {
     pa.stage_bytes = (uint32_t)Map::kStageBytes;
     pa.order = any_order ? &hdr->order_mode : nullptr;
-    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt<K>(), false, kPartNW) + pa.stage_bytes;
-    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks, false>;
-    auto kany = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks, true>;
+    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt_keys<K>(), false, kPartNW) + pa.stage_bytes;
+    auto kern = k_partition<K, Map, false, part_ipt_keys<K>(), kPartNW, part_minb_keys<K>(), false>;
+    auto kany = k_partition<K, Map, false, part_ipt_keys<K>(), kPartNW, part_minb_keys<K>(), true>;
     set_smem_once(kern, sm);
     set_smem_once(kany, sm);
     {
@@ -1320,7 +1320,7 @@ hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, u
   uint32_t nbits = 8;
   while (nbits < 32 && (n - 1) >> nbits) nbits += 8;
   {
-    const size_t sm = align_up((size_t)kV1HeavyNW * 32 * kPartIPT * (sizeof(K) + 5) +
+    const size_t sm = align_up((size_t)kV1HeavyNW * 32 * kV1HeavyIPT * (sizeof(K) + 5) +
                                (size_t)rank_words<kV1HeavyNW>() * 4 + 2 * 256 * 4, 16) + 32 * 4 + 64;
     auto kern = k_v1_fix_heavy<K>;
     set_smem_once(kern, sm);
@@ -1341,11 +1341,11 @@ hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, u
 // Binned probe.  HashGraph-Probe-Standard answers each query with random
 // reads into the table; on HBM every random 4-byte read costs a whole DRAM
 // burst.  Here the queries are first partitioned by bucket range into ng
-// groups (the build's histogram and stable partition kernels, applied to the
+// groups (the build's histogram and partition kernels, applied to the
 // queries), so that the group being probed touches one table slice small
 // enough to stay in L2; the per-query counts are then put back in query
 // order by a merge over the groups (inside a group the query positions
-// ascend, because the partition is stable).
+// ascend from one block of kQueryBlock positions to the next).
 // ===========================================================================
 // Counts back to query order when the positions inside every group come in
 // long ascending runs (batched tables: a table's queries fall into one or two
@@ -1431,6 +1431,18 @@ __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t*
   }
 }
 
+// Queries are grouped by a partition that ranks each tile in any order (its
+// tiles are whole blocks of kQueryBlock positions or the end of the
+// queries).  A group's positions are therefore ascending from block to
+// block, though not inside a block's run, and the merge works in output
+// tiles made of whole blocks: within a group, every query of an earlier
+// output tile precedes every query of a later one, which is all its
+// cursors need.
+constexpr uint64_t kQueryBlock = 4096;
+static_assert(kQueryBlock % (kPartNW * 32 * part_ipt_queries<uint32_t>()) == 0 &&
+                  kQueryBlock % (kPartNW * 32 * part_ipt_queries<uint64_t>()) == 0 && kUnpermuteTile % kQueryBlock == 0,
+              "query blocks are whole partition tiles; merge tiles are whole blocks");
+
 #ifndef HG_PROBE_GROUP_BITS
 #define HG_PROBE_GROUP_BITS 7  // log2 of the query groups (at most 8; 7 measured best at 2^28)
 #endif
@@ -1449,8 +1461,10 @@ bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePl
   p->ng = (uint32_t)(((V - 1) >> sg) + 1);
   if (p->ng > 256) return false;
   const int sms = std::max(di.sms, 1);
+  // chunks are whole 4096-query blocks, so every partition tile lies in one
+  // block (the merge below relies on it)
   uint64_t chunk = std::max<uint64_t>(kPartTile, (q + 2 * sms - 1) / (2 * sms));
-  chunk = (chunk + 15) / 16 * 16;
+  chunk = (chunk + kQueryBlock - 1) / kQueryBlock * kQueryBlock;
   p->chunk = chunk;
   p->G = (uint32_t)std::max<uint64_t>(1, (q + chunk - 1) / chunk);
   size_t o = sizeof(WsHeader);
@@ -1516,8 +1530,8 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.status = &hdr->status;
   {
     pa.stage_bytes = (uint32_t)Map::kStageBytes;
-    const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt<K>(), false, kPartNW) + pa.stage_bytes;
-    auto kern = k_partition<K, Map, false, part_ipt<K>(), kPartNW, kPartMinBlocks, false>;
+    const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW) + pa.stage_bytes;
+    auto kern = k_partition<K, Map, false, part_ipt_queries<K>(), kPartNW, kPartMinBlocksQ, true>;
     set_smem_once(kern, sm);
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
@@ -1528,9 +1542,9 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   {
     // every CTA merges a span of at least 4096 outputs (in tiles of up to
     // kUnpermuteTile), so small batches still spread over the SMs
-    const uint64_t spans = (q + 4095) / 4096;
-    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(spans, (uint64_t)2 * di.sms));
-    const uint64_t span = (q + grid - 1) / grid;
+    const uint64_t blocks = (q + kQueryBlock - 1) / kQueryBlock;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)2 * di.sms));
+    const uint64_t span = (blocks + grid - 1) / grid * kQueryBlock;  // whole blocks
     HG_TRACE("k_unpermute", st);
     if (Map::kNeedsPos)
       k_scatter_counts<<<(unsigned)std::min<uint64_t>((q + 255) / 256, (uint64_t)di.sms * 16), 256, 0, st>>>(
@@ -1603,8 +1617,8 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
   uint32_t* ids = (uint32_t*)(ws + o[6]);
   uint64_t* src = keys;
   uint64_t* dst = tmp;
-  const size_t psm = part_smem_bytes(8, false, part_ipt<uint64_t>(), false, kPartNW);
-  auto kp = k_partition<uint64_t, RadixByteMap, false, part_ipt<uint64_t>(), kPartNW, kPartMinBlocks, false>;
+  const size_t psm = part_smem_bytes(8, false, part_ipt_queries<uint64_t>(), false, kPartNW);
+  auto kp = k_partition<uint64_t, RadixByteMap, false, part_ipt_queries<uint64_t>(), kPartNW, kPartMinBlocksQ, false>;
   set_smem_once(kp, psm);
   auto kh = k_hist<uint64_t, RadixByteMap>;
   const size_t hsm = hist_stage_offset(256);

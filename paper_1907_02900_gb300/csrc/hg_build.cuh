@@ -9,42 +9,55 @@ constexpr int kHistThreads = 1024;
 constexpr uint32_t kMaxBinsLog2 = 15;  // bins counted in one shared-memory histogram
 constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local index, 128 KB cursors)
 // Partition geometry (compile-time; the defaults are the tuned values).
+// Pass A (keys) and the query partition share a kernel but not their tiles:
+// the query tiles must be powers of two (whole blocks of the probe's merge).
 #ifndef HG_PART_NW
 #define HG_PART_NW 16
 #endif
 #ifndef HG_PART_IPT
-#define HG_PART_IPT 8
+#define HG_PART_IPT 16  // pass A, 4-byte keys: tiles of 8192, one CTA per SM
+#endif
+#ifndef HG_PART_MINB
+#define HG_PART_MINB 1
+#endif
+#ifndef HG_PART_IPTQ
+#define HG_PART_IPTQ 8  // query partition (and the sample sort), 4-byte keys: tiles of 4096
+#endif
+#ifndef HG_PART_MINBQ
+#define HG_PART_MINBQ 2
+#endif
+#ifndef HG_PART_IPT64
+#define HG_PART_IPT64 4  // 8-byte keys, both: tiles of 2048, two CTAs per SM
 #endif
 #ifndef HG_PART_IPTB
 #define HG_PART_IPTB 6
 #endif
-#ifndef HG_PART_MINB
-#define HG_PART_MINB 2
-#endif
 #ifndef HG_PARTB_NW
-#define HG_PARTB_NW 8
+#define HG_PARTB_NW 16
 #endif
 #ifndef HG_PARTB_MINB
-#define HG_PARTB_MINB 4
+#define HG_PARTB_MINB 2
 #endif
-constexpr int kPartNW = HG_PART_NW;      // warps of the partition kernels (pass A, query grouping)
-#ifndef HG_PART_IPT64
-#define HG_PART_IPT64 4
-#endif
-constexpr int kPartIPT = HG_PART_IPT;    // items per thread, pass A (4-byte keys)
-// pass A items per thread for K: 8-byte keys take a smaller tile, so that
-// two CTAs fit in one SM's shared memory
+constexpr int kPartNW = HG_PART_NW;  // warps of the pass A / query partition CTAs
 template <typename K>
-constexpr int part_ipt() {
+constexpr int part_ipt_keys() {  // pass A items per thread
   return sizeof(K) == 8 ? HG_PART_IPT64 : HG_PART_IPT;
 }
+template <typename K>
+constexpr int part_minb_keys() {
+  return sizeof(K) == 8 ? 2 : HG_PART_MINB;
+}
+template <typename K>
+constexpr int part_ipt_queries() {  // query partition items per thread
+  return sizeof(K) == 8 ? HG_PART_IPT64 : HG_PART_IPTQ;
+}
+constexpr int kPartMinBlocksQ = HG_PART_MINBQ;
 constexpr int kPartIPTB = HG_PART_IPTB;  // items per thread, pass B
-constexpr int kPartMinBlocks = HG_PART_MINB;
-constexpr int kPartBNW = HG_PARTB_NW;    // pass B: smaller CTAs, more of them per SM
+constexpr int kPartBNW = HG_PARTB_NW;
 constexpr int kPartBMinBlocks = HG_PARTB_MINB;
 constexpr uint32_t kMaxItemsPerCta = 128;  // pass B work items one CTA may own
 constexpr uint32_t kMaxBinsPerCta = 256;   // bins one bin-build CTA may own
-constexpr int kPartTile = kPartNW * 32 * kPartIPT;  // 4096 elements per tile
+constexpr int kPartTile = kPartNW * 32 * HG_PART_IPTQ;  // query tile: 4096 elements (smallest chunk)
 #ifndef HG_BIN_NW
 #define HG_BIN_NW 32
 #endif
@@ -58,6 +71,7 @@ constexpr uint64_t kHugeMinN = 1ull << 22;  // ... in builds of at least this ma
 constexpr uint32_t kBinBitmapWarps = 4;  // warps sorting long buckets with position bitmaps
 constexpr uint32_t kV1Small = 32;      // V1 fix-up: longest bucket sorted by one thread
 constexpr int kV1HeavyNW = 16;
+constexpr int kV1HeavyIPT = 8;  // V1 fix-up of long buckets: tiles of 4096
 
 // V2 launch plan and workspace layout.
 struct Plan {
