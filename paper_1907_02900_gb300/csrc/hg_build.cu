@@ -1167,9 +1167,11 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.BS = BS;
   pa.status = status;
   {
-    pa.stage_bytes = (uint32_t)Map::kStageBytes;
+    // the map's tables are staged only where they fit next to the tile
+    const size_t own = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt_keys<K>(), false, kPartNW);
+    pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
     pa.order = any_order ? &hdr->order_mode : nullptr;
-    const size_t sm = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt_keys<K>(), false, kPartNW) + pa.stage_bytes;
+    const size_t sm = own + pa.stage_bytes;
     auto kern = k_partition<K, Map, false, part_ipt_keys<K>(), kPartNW, part_minb_keys<K>(), false>;
     auto kany = k_partition<K, Map, false, part_ipt_keys<K>(), kPartNW, part_minb_keys<K>(), true>;
     set_smem_once(kern, sm);
@@ -1529,8 +1531,9 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.BS = GS;
   pa.status = &hdr->status;
   {
-    pa.stage_bytes = (uint32_t)Map::kStageBytes;
-    const size_t sm = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW) + pa.stage_bytes;
+    const size_t own = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW);
+    pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
+    const size_t sm = own + pa.stage_bytes;
     auto kern = k_partition<K, Map, false, part_ipt_queries<K>(), kPartNW, kPartMinBlocksQ, true>;
     set_smem_once(kern, sm);
     HG_TRACE("k_partition_Q", st);

@@ -110,6 +110,13 @@ def test_learned_build_probe_join_match_oracle(hg, orc, lrn, kt):
         roff, rk, ri = orc.build(keys, V, model=blob)
         assert np.array_equal(off, roff) and np.array_equal(ck, rk) and np.array_equal(ci, ri)
     assert orc.check_table(off, ck, ci, keys, V, model=blob) == []
+    # explicit ids: stable partitions, and the pass whose tile leaves no room
+    # to stage the model in shared memory
+    ids = (np.arange(len(keys), dtype=np.uint64) * np.uint64(2654435761) % np.uint64(1 << 32)).astype(np.uint32)
+    ti = hg.build(to_dev(keys), V, model=model, ids=to_dev(ids))
+    got_i = table_np(ti)
+    want_i = orc.build(keys, V, model=blob, ids=ids)
+    assert all(np.array_equal(g, w) for g, w in zip(got_i, want_i))
     for binned in (False, True):
         got = to_np(hg.probe(t, to_dev(q), binned=binned))
         assert np.array_equal(got, orc.multiplicity(keys, q))
