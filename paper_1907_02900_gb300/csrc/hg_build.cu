@@ -47,7 +47,7 @@ size_t big_smem_bytes(int kb, uint32_t nb) { return align_up((size_t)nb * 4, 16)
 size_t part_smem_bytes(int kb, bool ids_in, int ipt, bool item_list, int nw) {
   const size_t tile = (size_t)nw * 32 * ipt;
   const size_t tb = tile + 16;
-  const size_t rw = nw == kPartNW ? (size_t)rank_words<kPartNW>() : (size_t)rank_words<kPartBNW>();
+  const size_t rw = (size_t)256 * (nw + 1 + (nw & 1));  // rank_words<nw>()
   size_t b = 2 * tb * kb + (ids_in ? 2 * tb * 4 : 0) + tile * (kb + 4 + 1) + rw * 4 +
              2 * 256 * 4;
   return align_up(b, 16) + (item_list ? 2 * kMaxItemsPerCta * 4 : 0) + 32 * 4 + 2 * 8 + 64;
@@ -1167,20 +1167,21 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   pa.BS = BS;
   pa.status = status;
   {
-    // the map's tables are staged only where they fit next to the tile
-    const size_t own = part_smem_bytes(sizeof(K), ids != nullptr, part_ipt_keys<K>(), false, kPartNW);
-    pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
     pa.order = any_order ? &hdr->order_mode : nullptr;
-    const size_t sm = own + pa.stage_bytes;
-    auto kern = k_partition<K, Map, false, part_ipt_keys<K>(), kPartNW, part_minb_keys<K>(), false>;
-    auto kany = k_partition<K, Map, false, part_ipt_keys<K>(), kPartNW, part_minb_keys<K>(), true>;
-    set_smem_once(kern, sm);
-    set_smem_once(kany, sm);
-    {
-      HG_TRACE("k_partition_A", st);
-      if (any_order) kany<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
-      kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
-    }
+    // the map's tables are staged only where they fit next to the tile
+    auto launch = [&](auto kern, int ipt) {
+      PartArgs<K> x = pa;
+      const size_t own = part_smem_bytes(sizeof(K), ids != nullptr, ipt, false, kPartNW);
+      x.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
+      set_smem_once(kern, own + x.stage_bytes);
+      kern<<<p.G, kPartNW * 32, own + x.stage_bytes, st>>>(x, map);
+    };
+    HG_TRACE("k_partition_A", st);
+    if (any_order)
+      launch(k_partition<K, Map, false, part_ipt_keys<K, true>(), kPartNW, part_minb_keys<K, true>(), true>,
+             part_ipt_keys<K, true>());
+    launch(k_partition<K, Map, false, part_ipt_keys<K, false>(), kPartNW, part_minb_keys<K, false>(), false>,
+           part_ipt_keys<K, false>());
   }
   if (two) {
     PartArgs<K> pb = pa;
@@ -1189,25 +1190,23 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     pb.out_k = bk;
     pb.out_i = bi;
     pb.stage_bytes = 0;  // (staging would cost pass B a resident CTA per SM)
-    const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true, kPartBNW);
-    auto kern = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks, false>;
-    auto kany = k_partition<K, Map, true, kPartIPTB, kPartBNW, kPartBMinBlocks, true>;
-    set_smem_once(kern, sm);
-    set_smem_once(kany, sm);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPartBNW * 32, sm);
     // ~32K edges per item: enough to amortise the per-item set-up
     const uint64_t per_chunk_sb = std::max<uint64_t>(1, p.n / ((uint64_t)p.G * p.nsb));
     pb.gg = (uint32_t)std::min<uint64_t>(p.G, std::max<uint64_t>(1, 32768 / per_chunk_sb));
     pb.ngroups = (p.G + pb.gg - 1) / pb.gg;
     const uint64_t items = (uint64_t)p.nsb * pb.ngroups;
-    unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)std::max(1, per_sm) * di.sms);
-    grid = (unsigned)std::max<uint64_t>(grid, (items + kMaxItemsPerCta - 1) / kMaxItemsPerCta);
-    {
-      HG_TRACE("k_partition_B", st);
-      if (any_order) kany<<<grid, kPartBNW * 32, sm, st>>>(pb, map);
-      kern<<<grid, kPartBNW * 32, sm, st>>>(pb, map);
-    }
+    auto launch = [&](auto kern, int nw) {
+      const size_t sm = part_smem_bytes(sizeof(K), true, kPartIPTB, true, nw);
+      set_smem_once(kern, sm);
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nw * 32, sm);
+      unsigned grid = (unsigned)std::min<uint64_t>(items, (uint64_t)std::max(1, per_sm) * di.sms);
+      grid = (unsigned)std::max<uint64_t>(grid, (items + kMaxItemsPerCta - 1) / kMaxItemsPerCta);
+      kern<<<grid, nw * 32, sm, st>>>(pb, map);
+    };
+    HG_TRACE("k_partition_B", st);
+    if (any_order) launch(k_partition<K, Map, true, kPartIPTB, partb_nw<true>(), partb_minb<true>(), true>, partb_nw<true>());
+    launch(k_partition<K, Map, true, kPartIPTB, partb_nw<false>(), partb_minb<false>(), false>, partb_nw<false>());
   }
   BinArgs<K> ba{};
   ba.in_k = bk;

@@ -11,14 +11,22 @@ constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local ind
 // Partition geometry (compile-time; the defaults are the tuned values).
 // Pass A (keys) and the query partition share a kernel but not their tiles:
 // the query tiles must be powers of two (whole blocks of the probe's merge).
+// The tile ranking in any order (k_partition ANY) and the stable ranking
+// are tuned separately: they cost different registers and instructions.
 #ifndef HG_PART_NW
 #define HG_PART_NW 16
 #endif
 #ifndef HG_PART_IPT
-#define HG_PART_IPT 16  // pass A, 4-byte keys: tiles of 8192, one CTA per SM
+#define HG_PART_IPT 16  // pass A, 4-byte keys, any order: tiles of 8192, one CTA per SM
 #endif
 #ifndef HG_PART_MINB
 #define HG_PART_MINB 1
+#endif
+#ifndef HG_PART_IPTS
+#define HG_PART_IPTS 16  // pass A, 4-byte keys, stable: tiles of 8192, one CTA per SM
+#endif
+#ifndef HG_PART_MINBS
+#define HG_PART_MINBS 1
 #endif
 #ifndef HG_PART_IPTQ
 #define HG_PART_IPTQ 8  // query partition (and the sample sort), 4-byte keys: tiles of 4096
@@ -27,34 +35,46 @@ constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local ind
 #define HG_PART_MINBQ 2
 #endif
 #ifndef HG_PART_IPT64
-#define HG_PART_IPT64 4  // 8-byte keys, both: tiles of 2048, two CTAs per SM
+#define HG_PART_IPT64 4  // 8-byte keys, everywhere: tiles of 2048, two CTAs per SM
 #endif
 #ifndef HG_PART_IPTB
-#define HG_PART_IPTB 6
+#define HG_PART_IPTB 6  // pass B items per thread
 #endif
 #ifndef HG_PARTB_NW
-#define HG_PARTB_NW 16
+#define HG_PARTB_NW 16  // pass B, any order: 512-thread CTAs, two per SM
 #endif
 #ifndef HG_PARTB_MINB
 #define HG_PARTB_MINB 2
 #endif
+#ifndef HG_PARTB_NWS
+#define HG_PARTB_NWS 8  // pass B, stable: 256-thread CTAs, up to four per SM
+#endif
+#ifndef HG_PARTB_MINBS
+#define HG_PARTB_MINBS 4
+#endif
 constexpr int kPartNW = HG_PART_NW;  // warps of the pass A / query partition CTAs
-template <typename K>
+template <typename K, bool ANY>
 constexpr int part_ipt_keys() {  // pass A items per thread
-  return sizeof(K) == 8 ? HG_PART_IPT64 : HG_PART_IPT;
+  return sizeof(K) == 8 ? HG_PART_IPT64 : ANY ? HG_PART_IPT : HG_PART_IPTS;
 }
-template <typename K>
+template <typename K, bool ANY>
 constexpr int part_minb_keys() {
-  return sizeof(K) == 8 ? 2 : HG_PART_MINB;
+  return sizeof(K) == 8 ? 2 : ANY ? HG_PART_MINB : HG_PART_MINBS;
 }
 template <typename K>
 constexpr int part_ipt_queries() {  // query partition items per thread
   return sizeof(K) == 8 ? HG_PART_IPT64 : HG_PART_IPTQ;
 }
 constexpr int kPartMinBlocksQ = HG_PART_MINBQ;
-constexpr int kPartIPTB = HG_PART_IPTB;  // items per thread, pass B
-constexpr int kPartBNW = HG_PARTB_NW;
-constexpr int kPartBMinBlocks = HG_PARTB_MINB;
+constexpr int kPartIPTB = HG_PART_IPTB;
+template <bool ANY>
+constexpr int partb_nw() {
+  return ANY ? HG_PARTB_NW : HG_PARTB_NWS;
+}
+template <bool ANY>
+constexpr int partb_minb() {
+  return ANY ? HG_PARTB_MINB : HG_PARTB_MINBS;
+}
 constexpr uint32_t kMaxItemsPerCta = 128;  // pass B work items one CTA may own
 constexpr uint32_t kMaxBinsPerCta = 256;   // bins one bin-build CTA may own
 constexpr int kPartTile = kPartNW * 32 * HG_PART_IPTQ;  // query tile: 4096 elements (smallest chunk)
