@@ -90,7 +90,11 @@ typedef struct {
  *   d_csr_keys out [n] keys grouped by bucket
  *   d_csr_ids  out [n] ids in the same order
  *   d_ws/ws_bytes  workspace of at least hg_build_workspace_size(cfg, n) bytes
- * Requires n < 2^32.  Output buffers must not overlap the inputs. */
+ * Requires n < 2^32.  Output buffers must not overlap the inputs.  The
+ * result is one canonical table whatever the configuration: inside every
+ * bucket the edges follow their input order (with d_ids NULL the build may
+ * partition in any order and restore it from the ids, which are then the
+ * positions). */
 size_t hg_build_workspace_size(const hg_config* cfg, uint64_t n);
 hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids, uint64_t n,
                    uint32_t* d_offsets, void* d_csr_keys, uint32_t* d_csr_ids, void* d_ws,
@@ -108,10 +112,11 @@ hg_status hg_probe(const hg_config* cfg, const hg_table* table, const void* d_qu
 
 /* Binned probe: the same result as hg_probe (per-query match counts), for
  * large query batches.  The queries are first partitioned by bucket range
- * into at most 256 groups (the V2 build's histogram and stable partition
- * applied to the queries), each group is probed while its slice of the table
- * stays in L2, and the counts are merged back into query order.  Trades
- * random DRAM reads (one burst per 4-byte read) for sequential passes.
+ * into at most 256 groups (128 by default; the V2 build's histogram and
+ * partition kernels applied to the queries), each group is probed while its
+ * slice of the table stays in L2, and the counts are merged back into query
+ * order.  Trades random DRAM reads (one burst per 4-byte read) for
+ * sequential passes.
  *   d_queries must be 16-byte aligned; q < 2^32.
  *   d_ws/ws_bytes: at least hg_probe_workspace_size(cfg, table->n, q) bytes. */
 size_t hg_probe_workspace_size(const hg_config* cfg, uint64_t table_n, uint64_t q);
