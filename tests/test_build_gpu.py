@@ -256,3 +256,20 @@ def test_build_probe_host_batches_in_flight(hg, orc):
         off, ck, ci = table_np(slots[i % 2]["t"])
         roff, rk, ri = orc.build(hosts[i][0], V)
         assert np.array_equal(off, roff) and np.array_equal(ck, rk) and np.array_equal(ci, ri), i
+
+
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+def test_any_order_tiles_equal_stable_build(hg, orc, kt):
+    """Implicit ids let the partitions rank tiles in any order (the bin build
+    restores input order from the ids); explicit ids equal to the positions
+    force the stable partitions.  Both must give the canonical table, byte
+    for byte, with buckets of many edges (ranked by id) included."""
+    n, V = (1 << 21) + 77, 1 << 20
+    keys = dg.uniform_keys_u32(n, 41) if kt == "u32" else dg.uniform_keys_u64(n, 41)
+    keys[:1500] = keys[1500]  # one bucket of 1501+ edges in a bin that still fits shared memory
+    t_any = hg.build(to_dev(keys), V)
+    t_stable = hg.build(to_dev(keys), V, ids=to_dev(np.arange(n, dtype=np.uint32)))
+    a, b = table_np(t_any), table_np(t_stable)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    roff, rk, ri = orc.build(keys, V)
+    assert np.array_equal(a[0], roff) and np.array_equal(a[1], rk) and np.array_equal(a[2], ri)
