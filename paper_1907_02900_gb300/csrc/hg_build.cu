@@ -4,15 +4,19 @@
 //   k_hist       per input chunk g: histogram of bins (bin = bucket >> s),
 //                bins held in shared memory (Alg. 2 Phase 1, "Bin Counting")
 //   k_colscan    per bin: exclusive prefix over chunks; bin totals
-//   k_scan_bins  exclusive scan of bin totals -> bin starts (Phase 2 prefix sum)
-//   k_partition  pass A: chunk -> super-bins (256-way stable partition);
-//                pass B: (super-bin, chunk) -> bins (<=256-way stable partition)
+//   k_scan_bins  exclusive scan of bin totals -> bin starts (Phase 2 prefix
+//                sum); the order mode (see below)
+//   k_partition  pass A: chunk -> super-bins (256-way partition);
+//                pass B: (super-bin, chunk) -> bins (<=256-way partition)
 //                (Phase 2, "Bin Placement and Data Reorganization")
-//   k_binbuild   per bin, in shared memory: local bucket index, stable counting
+//   k_binbuild   per bin, in shared memory: local bucket index, counting
 //                sort, CSR offsets and edges (Phase 3, "HashGraph Creation")
 //   k_binbuild_big  bins larger than shared memory, streamed by one CTA each
-// Every partition is stable, so the table comes out in the canonical order
-// (bucket, then input position) without atomics deciding any position.
+// The table comes out in the canonical order (bucket, then input position)
+// without atomics deciding any position: either both partitions are stable
+// and the bin build ranks each bucket by bin position, or (implicit ids and
+// every bin in shared memory: order mode 0) the partitions rank tiles in any
+// order and the bin build ranks each bucket by id, which is the position.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -271,9 +275,9 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
 // pass A's output, contiguous in memory; digit = bin inside the super-bin.
 // A group's elements are in input order, so one running cursor per bin,
 // started at the bin start plus the earlier chunks' counts, keeps the pass
-// stable.  Tiles stream through shared memory by TMA bulk copies,
-// double-buffered; each tile is stably partitioned and written out as
-// contiguous runs.
+// stable when its tiles are.  Tiles stream through shared memory by TMA bulk
+// copies, double-buffered; each tile is partitioned (stably, or in any order
+// with ANY) and written out as contiguous runs.
 template <typename K>
 struct PartArgs {
   const K* in_k;
@@ -516,9 +520,9 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 //   2. exclusive scan of the counts -> bucket starts, packed the same way
 //   3. every edge claims a slot of its bucket with an atomic increment; the
 //      slot order inside a bucket is arbitrary at this point
-//   4. every bucket sorts its slots by position in the bin, which is input
-//      order because both partition passes are stable: insertion sort for
-//      up to kBinSmallBucket edges, a per-warp position bitmap above
+//   4. buckets above kBinSmallBucket edges sort their slots by position in
+//      the bin (per-warp position bitmaps); the position is input order when
+//      both partition passes were stable
 //   5. the edges are written out in slot order, and the bin's offsets
 //      (both coalesced)
 // LB: the local buckets of step 1 are kept for step 3 (else recomputed).

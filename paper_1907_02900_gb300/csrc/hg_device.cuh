@@ -2,7 +2,7 @@
 //
 // Everything here is sm_103a device code: the Murmur3 bucket map (Eq. 1),
 // the learned bucket map, warp/block scans, the stable block-wide ranking
-// used by every partition step, and bounded TMA bulk-copy waits.
+// of the stable partition steps, and bounded TMA bulk-copy waits.
 #pragma once
 
 #include <cstdint>

@@ -1,5 +1,6 @@
-// Tile-level stable partition and in-shared-memory counting sorts, shared by
-// the build, the oversized-bin path and the V1 fix-up.
+// Tile-level partitions (stable, and in any order) and in-shared-memory
+// counting sorts, shared by the build, the query grouping, the oversized-bin
+// path and the V1 fix-up.
 #pragma once
 
 #include "hg_device.cuh"
