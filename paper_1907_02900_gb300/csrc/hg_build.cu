@@ -730,8 +730,11 @@ struct BinCfg {
   bool lb;
   size_t smem;
 };
+// Two 512-thread CTAs per SM (local buckets recomputed, no prefetch) measured
+// slower than one 1024-thread CTA that keeps them and prefetches the next bin
+// (2.42 against 2.27 ms at 2^28 keys); HG_BIN_TWO_PER_SM=1 selects them.
 #ifndef HG_BIN_TWO_PER_SM
-#define HG_BIN_TWO_PER_SM 1
+#define HG_BIN_TWO_PER_SM 0
 #endif
 static BinCfg bin_config(const Plan& p, bool recompute) {
   const DevInfo& di = dev_info();

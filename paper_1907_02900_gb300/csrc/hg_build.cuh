@@ -17,7 +17,7 @@ constexpr uint32_t kMaxBinShift = 15;  // buckets per bin <= 2^15 (u16 local ind
 #define HG_PART_NW 16
 #endif
 #ifndef HG_PART_IPT
-#define HG_PART_IPT 16  // pass A, 4-byte keys, any order: tiles of 8192, one CTA per SM
+#define HG_PART_IPT 20  // pass A, 4-byte keys, any order: tiles of 10240, one CTA per SM
 #endif
 #ifndef HG_PART_MINB
 #define HG_PART_MINB 1
