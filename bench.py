@@ -12,6 +12,8 @@ per step) exceed the 129 MB L2, so no flush is needed between steps.
 
 Other workloads (one JSON line each, same keys), chosen by --workload:
   plain    2^20 keys, 2^20 buckets, 2^20 queries (the oracle-sized case)
+  (scale and plain take --dup D: keys drawn uniformly from [1 .. N/D], an
+  average of D appearances per key, as in the duplicate-key experiment)
   join     Alg. 3: build 2^27 uint64 Zipf(1) keys over 2^24 values and 2^27
            uniform keys over the same values, join count and materialise
   batched  10,000 tables, log-uniform sizes scaled to a 2^30-key total, each
@@ -62,6 +64,9 @@ def parse():
     ap.add_argument("--standard-probe", action="store_true", help="time HashGraph-Probe-Standard instead of the binned probe")
     ap.add_argument("--algo", choices=["v2", "v1"], default="v2", help="build algorithm (Alg. 2 or Alg. 1)")
     ap.add_argument("--explicit-ids", action="store_true", help="build with a uint32 id array (+4 B read per key)")
+    ap.add_argument("--dup", type=float, default=0.0,
+                    help="scale/plain: keys drawn uniformly from [1 .. N/D], D appearances per key on average "
+                         "(the duplicate-key experiment); 0 = distinct-looking uniform keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
     ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed runs of the per-table loop")
@@ -312,13 +317,13 @@ class Ctx:
             raise RuntimeError(f"{where}: device status {self.hg.STATUS_NAMES.get(st, st)}")
 
 
-def oracle_sample(log2n: int, log2v: int, hit: float, seed: int):
+def oracle_sample(log2n: int, log2v: int, hit: float, seed: int, dup: float = 0.0):
     """Oracle (single-threaded CPU) build + probe of a bounded sample; returns (seconds, keys)."""
     import oracle
     from paper_1907_02900_gb300 import datagen as dg
     n = 1 << log2n
     V = 1 << log2v
-    keys = dg.uniform_keys_u32(n, seed)
+    keys = dg.dup_keys_u32(n, dup, seed) if dup > 0 else dg.uniform_keys_u32(n, seed)
     q = dg.queries_u32(n, keys, hit, seed + 1)
     oracle.build_oracle()
     t0 = time.perf_counter()
@@ -341,10 +346,10 @@ def run_reference(args):
     ln = min(args.cpu_log2n, args.log2n)
     lv = ln + (log2v_full - args.log2n)
     for _ in range(max(args.warmup, 0) and 1):
-        oracle_sample(ln - 4, lv - 4, args.hit, 7)
+        oracle_sample(ln - 4, lv - 4, args.hit, 7, args.dup)
     total_s, total_keys = 0.0, 0
     for i in range(args.steps):
-        s, k = oracle_sample(ln, lv, args.hit, 0x48470002 + i)
+        s, k = oracle_sample(ln, lv, args.hit, 0x48470002 + i, args.dup)
         total_s += s
         total_keys += k
     value = total_keys / total_s / 1e9
@@ -352,7 +357,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"oracle sample: 2^{ln} uint32 uniform keys, V=2^{lv}, probe 2^{ln} queries at "
+        "config": {"workload": f"oracle sample: 2^{ln} uint32 "
+                               f"{f'keys from [1 .. N/{args.dup:g}]' if args.dup > 0 else 'uniform keys'}, V=2^{lv}, probe 2^{ln} queries at "
                                f"{int(args.hit * 100)}% hits (same shape as 2^{args.log2n} keys, V=2^{log2v_full})",
                    "parallelism": "single-threaded CPU oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -372,7 +378,7 @@ def run_scale(c: Ctx):
     V = 1 << log2v
     q = n
     seed = dg.SEED_SCALE + 1000 * c.rank
-    keys_h = dg.uniform_keys_u32(n, seed)
+    keys_h = dg.dup_keys_u32(n, args.dup, seed) if args.dup > 0 else dg.uniform_keys_u32(n, seed)
     q_h = dg.queries_u32(q, keys_h, args.hit, seed + 1)
     keys_p = torch.from_numpy(keys_h.view(np.int32)).pin_memory()
     q_p = torch.from_numpy(q_h.view(np.int32)).pin_memory()
@@ -473,16 +479,21 @@ def run_scale(c: Ctx):
                "counts_returned": ok}
         del slots
 
+    # Duplicate keys come from [1 .. N/D] as raw values, so a miss query (a
+    # scrambled value from the upper half of the domain) can equal one of
+    # them with probability about (N/D) / 2^32: the hit rate is then slightly
+    # above the requested one.
+    key_kind = f"keys from [1 .. N/{args.dup:g}]" if args.dup > 0 else "uniform keys"
     cpu = None
     if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline:
         ln = min(args.cpu_log2n, args.log2n)
         lv = ln + (log2v - args.log2n)
-        secs, done = oracle_sample(ln, lv, args.hit, seed + 7)
-        cpu = cpu_line(secs, done, f"oracle build of 2^{ln} uint32 keys into 2^{lv} buckets + probe of 2^{ln} "
-                                   f"queries ({int(args.hit * 100)}% hits)")
+        secs, done = oracle_sample(ln, lv, args.hit, seed + 7, args.dup)
+        cpu = cpu_line(secs, done, f"oracle build of 2^{ln} uint32 {key_kind} into 2^{lv} buckets + probe of "
+                                   f"2^{ln} queries ({int(args.hit * 100)}% hits)")
     algo_name = "HashGraph-V2" if args.algo == "v2" else "HashGraph-V1"
     ids_name = "explicit uint32 ids" if args.explicit_ids else "implicit ids"
-    config = {"workload": f"{algo_name} build of 2^{args.log2n} uniform uint32 keys ({ids_name}) into 2^{log2v} "
+    config = {"workload": f"{algo_name} build of 2^{args.log2n} uint32 {key_kind} ({ids_name}) into 2^{log2v} "
                           f"buckets (murmur3) + {'binned probe' if binned else 'Probe-Standard'} of 2^{args.log2n} "
                           f"queries at {int(args.hit * 100)}% hits, per GPU",
               "global_batch": c.world * (n + q),
