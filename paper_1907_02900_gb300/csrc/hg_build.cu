@@ -504,6 +504,32 @@ struct recompute_bucket<MurmurMap> {
 };
 
 
+// Sorts the slots opos[beg, end) of one bucket (end - beg <= 32 * KR) by
+// position, with one warp: every lane holds up to KR positions, counts the
+// bucket's positions below each of them (all lanes read the same slot, a
+// broadcast) and, once every lane has read them all, stores each at its rank.
+// Positions are distinct, so the ranks are a permutation of the slots.
+template <int KR>
+__device__ __forceinline__ void warp_rank_positions(uint16_t* opos, uint32_t beg, uint32_t end, uint32_t lane) {
+  uint32_t p[KR], r[KR];
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const uint32_t i = beg + lane + 32u * k;
+    p[k] = i < end ? (uint32_t)opos[i] : 0xffffffffu;
+    r[k] = 0;
+  }
+  for (uint32_t i = beg; i < end; ++i) {
+    const uint32_t x = opos[i];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) r[k] += x < p[k];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < KR; ++k)
+    if (beg + lane + 32u * k < end) opos[beg + r[k]] = (uint16_t)p[k];
+  __syncwarp();
+}
+
 // Shared memory of k_binbuild: staging buffers of keys and ids, the local
 // bucket array (LB), slot order (u16), packed u16 bucket counters, the list
 // of long buckets, kBinBitmapWarps position bitmaps and small control state.
@@ -521,8 +547,9 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 //   3. every edge claims a slot of its bucket with an atomic increment; the
 //      slot order inside a bucket is arbitrary at this point
 //   4. buckets above kBinSmallBucket edges sort their slots by position in
-//      the bin (per-warp position bitmaps); the position is input order when
-//      both partition passes were stable
+//      the bin: up to kBinRankBucket edges one warp ranks a bucket's
+//      positions in registers, longer buckets use per-warp position bitmaps;
+//      the position is input order when both partition passes were stable
 //   5. the edges are written out in slot order, and the bin's offsets
 //      (both coalesced)
 // LB: the local buckets of step 1 are kept for step 3 (else recomputed).
@@ -649,8 +676,21 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     }
     __syncthreads();
     // 4. long buckets (every counter now holds its bucket's end): slots
-    //    sorted by position with per-warp position bitmaps
+    //    sorted by position, in registers by one warp per bucket (every warp
+    //    takes buckets) up to kBinRankBucket edges, else with per-warp
+    //    position bitmaps on the first NBM warps
     const uint32_t nh = *nheavy;
+    if (nh > 0) {
+      const uint32_t nw = blockDim.x >> 5;
+      for (uint32_t h = warp; h < nh; h += nw) {
+        const uint32_t v = heavy[h];
+        const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
+        const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
+        if (end - beg <= 64) warp_rank_positions<2>(opos, beg, end, lane);
+        else if (end - beg <= 128) warp_rank_positions<4>(opos, beg, end, lane);
+        else if (end - beg <= kBinRankBucket) warp_rank_positions<kBinRankBucket / 32>(opos, beg, end, lane);
+      }
+    }
     if (nh > 0 && warp < NBM) {
       // each of the first NBM warps owns one bitmap of E bits
       const uint32_t nbits_words = (E + 31) >> 5;
@@ -659,6 +699,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
         const uint32_t v = heavy[h];
         const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
         const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
+        if (end - beg <= kBinRankBucket) continue;  // ranked above
         for (uint32_t k = lane; k < nbits_words; k += 32) bm[k] = 0;
         __syncwarp();
         for (uint32_t i = beg + lane; i < end; i += 32) {

@@ -88,7 +88,8 @@ constexpr uint32_t kBinEmaxU64 = 7168;  // same for uint64 keys
 constexpr uint32_t kBinSmallBucket = 32; // bucket length sorted by one thread in the bin build
 constexpr uint32_t kHugeSeg = 1u << 17;  // bins above this many edges are built by several CTAs, one per segment
 constexpr uint64_t kHugeMinN = 1ull << 22;  // ... in builds of at least this many keys
-constexpr uint32_t kBinBitmapWarps = 4;  // warps sorting long buckets with position bitmaps
+constexpr uint32_t kBinRankBucket = 256; // longest bucket a warp ranks in registers in the bin build
+constexpr uint32_t kBinBitmapWarps = 4;  // warps sorting longer buckets with position bitmaps
 constexpr uint32_t kV1Small = 32;      // V1 fix-up: longest bucket sorted by one thread
 constexpr int kV1HeavyNW = 16;
 constexpr int kV1HeavyIPT = 8;  // V1 fix-up of long buckets: tiles of 4096

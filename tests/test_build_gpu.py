@@ -53,6 +53,24 @@ def test_build_duplicates(hg, orc, algo, mult):
     _check_build(hg, orc, dg.dup_keys_u32(400_000, mult, 6), 1 << 19, algo=algo)
 
 
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("explicit", [False, True])
+def test_build_long_buckets_every_sort_tier(hg, orc, kt, explicit):
+    """Buckets of 33 .. 300 edges in bins that fit shared memory: the bin
+    build sorts them by position in registers (up to 64, 128 and 256 edges)
+    or with bitmaps (longer).  Explicit ids keep the stable partitions; with
+    implicit ids the partitions may rank in any order and every bucket is
+    ranked by id."""
+    lens = np.array([33, 47, 64, 65, 100, 128, 129, 200, 255, 256, 257, 300], dtype=np.int64)
+    distinct = dg.uniform_keys_u32(6000, 12) if kt == "u32" else dg.uniform_keys_u64(6000, 12)
+    counts = np.ones(len(distinct), dtype=np.int64)
+    counts[:20 * len(lens)] = np.tile(lens, 20)
+    keys = np.repeat(distinct, counts)
+    keys = keys[np.random.default_rng(13).permutation(len(keys))]
+    ids = np.arange(len(keys), dtype=np.uint32) if explicit else None
+    _check_build(hg, orc, keys, 1 << 14, algo="v2", bin_shift=10, ids=ids)
+
+
 def test_build_all_keys_equal_and_single_bucket(hg, orc):
     keys = np.full(70_000, 123456789, dtype=np.uint32)
     for algo in ("v1", "v2"):
