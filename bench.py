@@ -69,6 +69,8 @@ def parse():
                          "(the duplicate-key experiment); 0 = distinct-looking uniform keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
+    ap.add_argument("--cpu-mt-log2n", type=int, default=24,
+                    help="sample size of the multithreaded CPU HashGraph (log2 keys); 0 = skip it")
     ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed runs of the per-table loop")
     a = ap.parse_args()
     if a.log2n is None:
@@ -332,6 +334,33 @@ def oracle_sample(log2n: int, log2v: int, hit: float, seed: int, dup: float = 0.
     return time.perf_counter() - t0, 2 * n
 
 
+def cpu_mt_sample(log2n: int, log2v: int, hit: float, seed: int, dup: float = 0.0) -> dict:
+    """The multithreaded CPU HashGraph (all host cores) on a bounded sample of
+    the workload: build + probe, median of three runs after a warm-up.  Never
+    raises: a failure is reported in the line instead."""
+    try:
+        import cpu_baseline as cmt
+        from paper_1907_02900_gb300 import datagen as dg
+        n, V = 1 << log2n, 1 << log2v
+        keys = dg.dup_keys_u32(n, dup, seed) if dup > 0 else dg.uniform_keys_u32(n, seed)
+        q = dg.queries_u32(n, keys, hit, seed + 1)
+        threads = cmt.max_threads()
+        off, ck, _ = cmt.build(keys[: 1 << 16], 1 << 16, threads=threads)
+        cmt.probe(off, ck, 1 << 16, q[: 1 << 16], threads=threads)
+        secs = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            off, ck, _ = cmt.build(keys, V, threads=threads)
+            cmt.probe(off, ck, V, q, threads=threads)
+            secs.append(time.perf_counter() - t0)
+        t = sorted(secs)[1]
+        return {"value": 2 * n / t / 1e9, "unit": UNIT, "cores": threads, "kind": "openmp HashGraph-V2",
+                "sample": f"build of 2^{log2n} uint32 keys into 2^{log2v} buckets + probe of 2^{log2n} queries "
+                          f"({int(hit * 100)}% hits), median of 3: {t:.3f} s; nproc={os.cpu_count()}"}
+    except Exception as e:  # the GPU line must not depend on the CPU comparison
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
+
 def cpu_line(secs: float, units: float, sample: str) -> dict:
     return {"value": units / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{sample}, {secs:.1f} s single-threaded; nproc={os.cpu_count()}"}
@@ -491,6 +520,10 @@ def run_scale(c: Ctx):
         secs, done = oracle_sample(ln, lv, args.hit, seed + 7, args.dup)
         cpu = cpu_line(secs, done, f"oracle build of 2^{ln} uint32 {key_kind} into 2^{lv} buckets + probe of "
                                    f"2^{ln} queries ({int(args.hit * 100)}% hits)")
+    cpu_mt = None
+    if c.rank == 0 and c.world == 1 and not args.no_cpu_baseline and args.cpu_mt_log2n > 0:
+        ln = min(args.cpu_mt_log2n, args.log2n)
+        cpu_mt = cpu_mt_sample(ln, ln + (log2v - args.log2n), args.hit, seed + 9, args.dup)
     algo_name = "HashGraph-V2" if args.algo == "v2" else "HashGraph-V1"
     ids_name = "explicit uint32 ids" if args.explicit_ids else "implicit ids"
     config = {"workload": f"{algo_name} build of 2^{args.log2n} uint32 {key_kind} ({ids_name}) into 2^{log2v} "
@@ -508,6 +541,7 @@ def run_scale(c: Ctx):
                   probe_gkeys_s=round(q / (probe_ms * 1e-3) / 1e9, 3) if probe_ms else None,
                   end_to_end_min_bytes_frac=round(min_bytes / (ms_per_step * 1e-3) / 1e9 / c.hbm, 4),
                   probe="binned" if binned else "standard", roofline=roof, phases=phases, cpu_baseline=cpu,
+                  cpu_mt_baseline=cpu_mt,
                   e2e=e2e, gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
 
 

@@ -30,7 +30,8 @@ def _worker(rank, world, port, out):
 
 def test_whole_job_rate_two_ranks():
     port = _free_port()
-    with mp.Manager() as m:
+    # spawn, not fork: earlier tests may have left threads (OpenMP, CUDA) in this process
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         for r in range(2):
