@@ -230,6 +230,8 @@ def build(keys, num_buckets: int, ids=None, seed: int = 0, algo: str = "auto", m
     torch = _torch()
     _require_cuda(keys, "keys")
     _require_cuda(ids, "ids")
+    if ids is not None and (ids.dtype not in (torch.uint32, torch.int32) or ids.numel() != keys.numel()):
+        raise ValueError("ids must be a 32-bit integer tensor with one entry per key")
     kt = _key_type_of(keys)
     cfg = make_config(kt, num_buckets, seed, algo, model, bin_shift)
     n = keys.numel()
