@@ -578,7 +578,8 @@ def run_join(c: Ctx):
         hg.build_into(cfg, a_d, None, tA.offsets, tA.keys, tA.ids, ws, c.stream)
         hg.build_into(cfg, b_d, None, tB.offsets, tB.keys, tB.ids, ws, c.stream)
         hg.join_count_into(tA, tB, total, None, jws, c.stream)
-        hg.join_materialize_into(tA, tB, out_a, out_b, total, jws, c.stream)
+        # the pairs are written from the per-edge counts the count pass left in jws
+        hg.join_materialize_into(tA, tB, out_a, out_b, total, jws, c.stream, after_count=True)
 
     for _ in range(args.warmup):
         step()
@@ -591,7 +592,6 @@ def run_join(c: Ctx):
     # two builds per step
     algo = {k: 2 * v for k, v in algo_build(8, n, V).items()}
     algo.update(algo_join(8, n, n, V, M))
-    algo["k_join_elem"] = 2 * algo["k_join_elem"]     # once for the count, once for the materialisation
     units = {k: 2 * n if k in algo_build(8, 1, 1) or k == "k_join_elem" else n for k in algo}
     roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
     join_ms = sum(prof[k][0] for k in prof if k.startswith("k_join") or k.startswith("k_scan")) / args.steps

@@ -175,12 +175,25 @@ hg_status hg_selftest_wait_timeout(void* d_ws, uint32_t limit_ms, void* stream);
  *                    device status is HG_ERR_OVERFLOW)
  * Both need hg_join_workspace_size(cfg, A->n, B->n) bytes of workspace. */
 size_t hg_join_workspace_size(const hg_config* cfg, uint64_t nA, uint64_t nB);
+/* hg_join_materialize_after_count: hg_join_materialize for a pair of tables
+ * that hg_join_count has just counted with the same workspace.  The count
+ * leaves every A edge's match count in the workspace; this call scans those
+ * into output positions and writes the pairs, so a count followed by the
+ * materialisation intersects the buckets once, not twice.  Neither table
+ * nor the workspace may change in between.  The device checks that the
+ * workspace holds the count of these tables (A and B sizes, offsets and keys
+ * pointers, V): on a mismatch it writes no pair, *d_total = 0 and the
+ * workspace status reads HG_ERR_INVALID_ARG.  The counts are consumed: a
+ * second call without a new count is a mismatch. */
 hg_status hg_join_count(const hg_config* cfg, const hg_table* A, const hg_table* B,
                         int64_t* d_total, int64_t* d_bucket_counts, void* d_ws, size_t ws_bytes,
                         void* stream);
 hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_table* B,
                               int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
                               int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream);
+hg_status hg_join_materialize_after_count(const hg_config* cfg, const hg_table* A, const hg_table* B,
+                                          int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
+                                          int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream);
 
 /* -------------------------------------------------------------- learned --
  * Learned bucket map: an order-preserving stand-in for "hash(a) mod V".  It
@@ -232,6 +245,27 @@ hg_status hg_learned_leaf_grad(int32_t key_type, const uint64_t* d_sorted, uint6
                                void* d_ws, size_t ws_bytes, void* stream);
 hg_status hg_bucket_stats(const hg_config* cfg, const void* d_keys, uint64_t n, uint32_t* d_counts,
                           double* d_out4, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Fallback rule of the learned map (not in the paper): Murmur is its judge.
+ * Both maps are applied to the same n keys (hg_bucket_stats with cfg's
+ * learned model, then with Murmur and cfg->seed); the learned map is kept
+ * (*h_keep = 1) while its bucket-length variance is at most var_tolerance
+ * times Murmur's and its longest bucket at most max_factor times Murmur's,
+ * else *h_keep = 0 and the caller builds with Murmur.  A strict "no worse
+ * than Murmur" rule would never keep it: Murmur's balls-into-bins variance
+ * equals the load factor, and a CDF fitted to a sample cannot beat that on
+ * fresh keys.  Tolerances <= 0 select the defaults below.
+ *   cfg        map = HG_MAP_LEARNED, d_model, num_buckets V, seed (for Murmur)
+ *   d_counts   V uint32 scratch;  d_ws/ws_bytes >= hg_learned_judge_workspace_size()
+ *   h_stats8   optional host out: learned {max, mean, variance, non-empty
+ *              buckets}, then Murmur's
+ * Synchronous: returns after `stream` has finished both statistics. */
+#define HG_LEARNED_VAR_TOLERANCE 1.25
+#define HG_LEARNED_MAX_FACTOR 4.0
+size_t hg_learned_judge_workspace_size(void);
+hg_status hg_learned_judge(const hg_config* cfg, const void* d_keys, uint64_t n, double var_tolerance,
+                           double max_factor, uint32_t* d_counts, void* d_ws, size_t ws_bytes, double* h_stats8,
+                           int32_t* h_keep, void* stream);
 
 /* -------------------------------------------------------------- batched --
  * Many independent tables of uneven sizes built and probed together.  The
@@ -309,17 +343,27 @@ hg_status hg_batch_run_plain(hg_batch_plan* plan, const void* d_keys, const void
  * bytes (8 MiB) per GPU that loads the library, held until the process exits.
  *   Same arguments and results as hg_build, without the workspace.
  *   Requests whose V2 plan needs more scratch than the array holds (more
- *   than hg_static_scratch_bytes() from hg_build_workspace_size; up to 2^18
- *   keys always fit for V <= 2^29) return HG_ERR_WORKSPACE_TOO_SMALL;
+ *   than hg_static_scratch_bytes() from hg_build_workspace_size; with the
+ *   automatic bin size, cfg->bin_shift = 0, up to 2^18 keys always fit for
+ *   V <= 2^29 with uint32 keys and V <= 2^28 with uint64 keys) return
+ *   HG_ERR_WORKSPACE_TOO_SMALL;
  *   cfg->algo == HG_ALGO_V1 returns HG_ERR_UNSUPPORTED.
  *   The first call on a device looks up the array's device address; make it
- *   before any stream capture.  All calls share the one array and it keeps
- *   the last call's contents: calls whose GPU work overlaps race, so
- *   serialise them (one stream, or host-side ordering). */
+ *   before any stream capture (a first call inside a capture returns
+ *   HG_ERR_UNSUPPORTED).  Calls on a stream that is not capturing look the
+ *   address up again, so a device reset between calls is harmless.  All
+ *   calls share the one array and it keeps the last call's contents: calls
+ *   whose GPU work overlaps race, so serialise them (one stream, or
+ *   host-side ordering).
+ * hg_static_scratch_status: the device status word the last build left in
+ *   the array (HG_OK, or HG_ERR_TIMEOUT / HG_ERR_OVERFLOW when the table is
+ *   not valid).  Synchronises `stream` first; allocates nothing.  The next
+ *   build clears it. */
 size_t hg_static_scratch_bytes(void);
 hg_status hg_build_static_scratch(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids,
                                   uint64_t n, uint32_t* d_offsets, void* d_csr_keys,
                                   uint32_t* d_csr_ids, void* stream);
+hg_status hg_static_scratch_status(void* stream);
 
 /* --------------------------------------------------------------- status --
  * Device status word of a workspace (HG_OK when no device-side error was

@@ -68,6 +68,8 @@ SIGNATURES = {
     "hg_learned_leaf_grad": (_I32, [_I32, _VP, _U64, _U64, ctypes.c_float, ctypes.c_float, _U32, _VP, _VP, _VP,
                                     _VP, _VP, _SZ, _VP]),
     "hg_bucket_stats": (_I32, [_CFGP, _VP, _U64, _VP, _VP, _VP, _SZ, _VP]),
+    "hg_learned_judge_workspace_size": (_SZ, []),
+    "hg_learned_judge": (_I32, [_CFGP, _VP, _U64, ctypes.c_double, ctypes.c_double, _VP, _VP, _SZ, _VP, _VP, _VP]),
     "hg_batch_plan_create": (_I32, [_I32, _U32, _U32, _VP, _VP, _VP, ctypes.POINTER(_VP)]),
     "hg_batch_plan_destroy": (None, [_VP]),
     "hg_batch_layout": (_I32, [_VP, _VP, _VP, _VP, _VP]),
@@ -80,10 +82,12 @@ SIGNATURES = {
     "hg_batch_run_eager": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_static_scratch_bytes": (_SZ, []),
     "hg_build_static_scratch": (_I32, [_CFGP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
+    "hg_static_scratch_status": (_I32, [_VP]),
     "hg_build_probe_host": (_I32, [_CFGP, _VP, _U64, _VP, _U64, _VP, _VP, _VP, _VP, _TABP, _VP, _SZ, _VP, _SZ, _VP]),
     "hg_join_workspace_size": (_SZ, [_CFGP, _U64, _U64]),
     "hg_join_count": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _VP, _SZ, _VP]),
     "hg_join_materialize": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
+    "hg_join_materialize_after_count": (_I32, [_CFGP, _TABP, _TABP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
     "hg_selftest_wait_timeout": (_I32, [_VP, _U32, _VP]),
     "hg_workspace_status": (_I32, [_VP, _VP]),
     "hg_workspace_clear": (_I32, [_VP, _VP]),
@@ -335,23 +339,28 @@ def join_count(A: Table, B: Table, per_bucket: bool = True, stream=None, ws=None
     return total, bc
 
 
-def join_materialize(A: Table, B: Table, capacity: int | None = None, stream=None, ws=None):
-    """Alg. 3 with the pairs written out: (A ids, B ids) int64 in canonical order."""
+def join_materialize(A: Table, B: Table, capacity: int | None = None, stream=None, ws=None,
+                     after_count: bool = False):
+    """Alg. 3 with the pairs written out: (A ids, B ids) int64 in canonical order.
+    Without a capacity the join is counted first (hg_join_count) in the same
+    workspace and the pairs are written from that count's per-edge match counts
+    (hg_join_materialize_after_count), so the buckets are intersected once.
+    after_count=True says that ws already holds hg_join_count's result for A and B."""
     torch = _torch()
     _same_space(A, B)
     dev = A.keys.device
-    if capacity is None:
-        capacity = int(join_count(A, B, per_bucket=False, stream=stream)[0].item())
     need = join_workspace_size(A.cfg, A.keys.numel(), B.keys.numel())
     if ws is None or ws.numel() < need:
+        if after_count:
+            raise ValueError("after_count needs the workspace of the preceding join_count")
         ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    if capacity is None:
+        capacity = int(join_count(A, B, per_bucket=False, stream=stream, ws=ws)[0].item())
+        after_count = True
     oa = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
     ob = torch.empty(max(capacity, 1), dtype=torch.int64, device=dev)
     total = torch.empty(1, dtype=torch.int64, device=dev)
-    ta, tb = A.view(), B.view()
-    rc = load().hg_join_materialize(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(oa), _ptr(ob),
-                                    capacity, _ptr(total), _ptr(ws), ws.numel(), _stream_handle(stream))
-    _check(rc, "hg_join_materialize")
+    join_materialize_into(A, B, oa, ob, total, ws, stream, after_count=after_count, capacity=capacity)
     m = min(int(total.item()), capacity)
     return oa[:m], ob[:m]
 
@@ -364,13 +373,19 @@ def join_count_into(A: Table, B: Table, total, bucket_counts, ws, stream=None):
                                 _ptr(bucket_counts), _ptr(ws), ws.numel(), _stream_handle(stream)), "hg_join_count")
 
 
-def join_materialize_into(A: Table, B: Table, out_a, out_b, total, ws, stream=None):
-    """hg_join_materialize on caller-provided tensors; capacity = out_a.numel()."""
+def join_materialize_into(A: Table, B: Table, out_a, out_b, total, ws, stream=None, after_count: bool = False,
+                          capacity: int | None = None):
+    """hg_join_materialize (or, after_count=True, hg_join_materialize_after_count,
+    which reuses the per-edge counts hg_join_count left in ws) on caller-provided
+    tensors; capacity defaults to out_a.numel()."""
     _same_space(A, B)
     ta, tb = A.view(), B.view()
-    _check(load().hg_join_materialize(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(out_a),
-                                      _ptr(out_b), out_a.numel(), _ptr(total), _ptr(ws), ws.numel(),
-                                      _stream_handle(stream)), "hg_join_materialize")
+    lib = load()
+    fn, name = ((lib.hg_join_materialize_after_count, "hg_join_materialize_after_count") if after_count
+                else (lib.hg_join_materialize, "hg_join_materialize"))
+    cap = out_a.numel() if capacity is None else capacity
+    _check(fn(ctypes.byref(A.cfg), ctypes.byref(ta), ctypes.byref(tb), _ptr(out_a), _ptr(out_b), cap, _ptr(total),
+              _ptr(ws), ws.numel(), _stream_handle(stream)), name)
 
 
 def selftest_wait_timeout(ws, limit_ms: int = 50, stream=None):
@@ -465,21 +480,27 @@ def bucket_stats(keys, num_buckets: int, model=None, seed: int = 0, stream=None)
     return {"max": float(o[0]), "mean": float(o[1]), "var": float(o[2]), "nonempty": float(o[3])}
 
 
-# Fallback rule of the learned map: Murmur judges it.  The learned map is
-# kept only while its bucket lengths stay close to Murmur's on the same keys.
-LEARNED_VAR_TOLERANCE = 1.25   # variance at most this multiple of Murmur's
-LEARNED_MAX_FACTOR = 4.0       # longest bucket at most this multiple of Murmur's
-
-
-def choose_map(keys, num_buckets: int, model, seed: int = 0, var_tolerance: float = LEARNED_VAR_TOLERANCE,
-               max_factor: float = LEARNED_MAX_FACTOR, stream=None):
-    """(model or None, report): the learned model if its bucket-length variance
-    and maximum over `keys` stay within the tolerances of Murmur's, else None
-    (use Murmur).  Both maps are evaluated on the GPU (hg_bucket_stats)."""
-    sl = bucket_stats(keys, num_buckets, model=model, stream=stream)
-    sm = bucket_stats(keys, num_buckets, seed=seed, stream=stream)
-    keep = sl["var"] <= var_tolerance * sm["var"] and sl["max"] <= max_factor * sm["max"]
-    return (model if keep else None), {"learned": sl, "murmur": sm, "kept": bool(keep)}
+def choose_map(keys, num_buckets: int, model, seed: int = 0, var_tolerance: float = 0.0,
+               max_factor: float = 0.0, stream=None):
+    """(model or None, report): Murmur judges the learned map on `keys`
+    (hg_learned_judge): the model is returned while the library keeps it,
+    else None (build with Murmur).  Tolerances <= 0 take the library's
+    defaults.  report: both maps' bucket-length statistics and the verdict."""
+    torch = _torch()
+    _require_cuda(keys, "keys")
+    lib = load()
+    cfg = make_config(_key_type_of(keys), num_buckets, seed, "auto", model)
+    counts = torch.empty(num_buckets, dtype=torch.uint32, device=keys.device)
+    ws = torch.empty(int(lib.hg_learned_judge_workspace_size()), dtype=torch.uint8, device=keys.device)
+    st = (ctypes.c_double * 8)()
+    keep = ctypes.c_int32(0)
+    _check(lib.hg_learned_judge(ctypes.byref(cfg), _ptr(keys), keys.numel(), var_tolerance, max_factor, _ptr(counts),
+                                _ptr(ws), ws.numel(), st, ctypes.byref(keep), _stream_handle(stream)),
+           "hg_learned_judge")
+    names = ("max", "mean", "var", "nonempty")
+    rep = {"learned": {k: float(st[i]) for i, k in enumerate(names)},
+           "murmur": {k: float(st[4 + i]) for i, k in enumerate(names)}, "kept": bool(keep.value)}
+    return (model if keep.value else None), rep
 
 
 class BatchPlan:

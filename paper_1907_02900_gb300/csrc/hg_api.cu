@@ -287,7 +287,26 @@ hg_status hg_join_materialize(const hg_config* cfg, const hg_table* A, const hg_
   return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
     using K = decltype(k);
     return join_materialize_impl<K>(cfg, A, B, d_build_ids, d_probe_ids, capacity, d_total, (uint8_t*)d_ws, st,
-                                    map);
+                                    map, false);
+  });
+}
+
+hg_status hg_join_materialize_after_count(const hg_config* cfg, const hg_table* A, const hg_table* B,
+                                          int64_t* d_build_ids, int64_t* d_probe_ids, uint64_t capacity,
+                                          int64_t* d_total, void* d_ws, size_t ws_bytes, void* stream) {
+  hg_status rc = check_join_args(cfg, A, B, d_ws);
+  if (rc != HG_OK) return rc;
+  if (!d_total || !aligned(d_total, 8)) return HG_ERR_INVALID_ARG;
+  if (capacity > 0 && (!d_build_ids || !d_probe_ids)) return HG_ERR_INVALID_ARG;
+  if (!aligned(d_build_ids, 8) || !aligned(d_probe_ids, 8)) return HG_ERR_INVALID_ARG;
+  if (ws_bytes < join_workspace_bytes(A->n, cfg->num_buckets)) return HG_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // only the status word is cleared: the rest of the header holds the count's stamp
+  if (cudaMemsetAsync(d_ws, 0, sizeof(uint32_t), st) != cudaSuccess) return HG_ERR_CUDA;
+  return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
+    using K = decltype(k);
+    return join_materialize_impl<K>(cfg, A, B, d_build_ids, d_probe_ids, capacity, d_total, (uint8_t*)d_ws, st,
+                                    map, true);
   });
 }
 

@@ -180,5 +180,5 @@ hg_status join_count_impl(const hg_config* cfg, const hg_table* A, const hg_tabl
 template <typename K, typename Map>
 hg_status join_materialize_impl(const hg_config* cfg, const hg_table* A, const hg_table* B, int64_t* outA,
                                 int64_t* outB, uint64_t cap, int64_t* d_total, uint8_t* ws, cudaStream_t st,
-                                Map map);
+                                Map map, bool after_count);
 }  // namespace hg

@@ -16,7 +16,9 @@ struct WsHeader {
   uint32_t order_mode;  // V2 build with implicit ids: 0 = partitions may rank tiles in any
                         // order (every bin fits shared memory), 1 = stable partitions needed
   uint64_t counters[8]; // scratch counters for kernels
-  uint8_t reserved[256 - 16 - 64];
+  uint64_t join_stamp[8];  // hg_join_count: the tables whose per-edge match counts the workspace holds
+  uint32_t join_abort;     // hg_join_materialize_after_count: the stamp did not match, write nothing
+  uint8_t reserved[256 - 16 - 64 - 64 - 4];
 };
 static_assert(sizeof(WsHeader) == 256, "workspace header");
 

@@ -58,11 +58,33 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_elem(const uint32_t* __re
 
 // Light buckets: one thread sums m over the bucket's A edges.  Every bucket
 // then adds its count to the block's share of the join total.
+// Which tables a workspace's per-edge match counts belong to: written by the
+// count, checked by the materialisation that reuses them.
+struct JoinStamp {
+  uint64_t w[8];
+};
+constexpr uint64_t kJoinStampMagic = 0x544E434E494F4A48ull;  // "HJOINCNT"
+
+static JoinStamp join_stamp(const hg_table* A, const hg_table* B, uint64_t V) {
+  JoinStamp s{};
+  s.w[0] = kJoinStampMagic;
+  s.w[1] = A->n;
+  s.w[2] = B->n;
+  s.w[3] = V;
+  s.w[4] = (uint64_t)(uintptr_t)A->d_offsets;
+  s.w[5] = (uint64_t)(uintptr_t)A->d_keys;
+  s.w[6] = (uint64_t)(uintptr_t)B->d_offsets;
+  s.w[7] = (uint64_t)(uintptr_t)B->d_keys;
+  return s;
+}
+
 __global__ void __launch_bounds__(kJoinThreads) k_join_bucket(const uint32_t* __restrict__ offA, uint64_t V,
                                                               const uint64_t* __restrict__ m,
                                                               unsigned long long* __restrict__ bucket_counts,
-                                                              unsigned long long* __restrict__ total) {
+                                                              unsigned long long* __restrict__ total,
+                                                              JoinStamp stamp, uint64_t* __restrict__ stamp_out) {
   __shared__ unsigned long long wsum[32];
+  if (blockIdx.x == 0 && threadIdx.x < 8) stamp_out[threadIdx.x] = stamp.w[threadIdx.x];
   unsigned long long acc = 0;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t s = offA[v], e = offA[v + 1];
@@ -119,9 +141,10 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(const K* __restrict
                                                              const uint64_t* __restrict__ moff,
                                                              int64_t* __restrict__ outA,
                                                              int64_t* __restrict__ outB, uint64_t cap,
-                                                             Map map) {
+                                                             const uint32_t* __restrict__ abort, Map map) {
   __shared__ int64_t stage_a[kJoinThreads / 32][kJoinWin];
   __shared__ int64_t stage_b[kJoinThreads / 32][kJoinWin];
+  if (*(volatile const uint32_t*)abort) return;
   map.init();
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   int64_t* sa = stage_a[w];
@@ -167,10 +190,28 @@ __global__ void __launch_bounds__(kJoinThreads) k_join_write(const K* __restrict
 }
 
 __global__ void k_join_finish(const uint64_t* __restrict__ moff, uint64_t nA, uint64_t cap,
-                              int64_t* __restrict__ d_total, uint32_t* status) {
+                              int64_t* __restrict__ d_total, uint32_t* status, const uint32_t* abort,
+                              uint64_t* stamp) {
+  stamp[0] = 0;  // the per-edge counts are now output positions: no later call may reuse them
+  if (*abort) {
+    *d_total = 0;
+    return;
+  }
   const uint64_t t = moff[nA];
   *d_total = (int64_t)t;
   if (t > cap) set_status(status, HG_ERR_OVERFLOW);
+}
+
+// The materialisation after a count: the workspace must hold the per-edge
+// match counts of exactly these tables (stamp).  On a mismatch nothing is
+// written and the status reads HG_ERR_INVALID_ARG.
+__global__ void k_join_check(JoinStamp want, const uint64_t* __restrict__ stamp, uint32_t* abort,
+                             uint32_t* status, uint64_t* __restrict__ moff, uint64_t nA) {
+  bool ok = true;
+  for (int i = 0; i < 8; ++i) ok &= stamp[i] == want.w[i];
+  *abort = ok ? 0u : 1u;
+  if (ok) moff[nA] = 0;  // closing element of the exclusive scan over nA + 1 entries
+  else set_status(status, HG_ERR_INVALID_ARG);
 }
 
 struct JoinWs {
@@ -212,38 +253,49 @@ hg_status join_count_impl(const hg_config* cfg, const hg_table* A, const hg_tabl
   const unsigned gb = (unsigned)std::min<uint64_t>((V + kJoinThreads - 1) / kJoinThreads, (uint64_t)sms * 16);
   {
     HG_TRACE("k_join_bucket", st);
-    k_join_bucket<<<gb, kJoinThreads, 0, st>>>(A->d_offsets, V, w.moff, bc, (unsigned long long*)d_total);
+    k_join_bucket<<<gb, kJoinThreads, 0, st>>>(A->d_offsets, V, w.moff, bc, (unsigned long long*)d_total,
+                                               join_stamp(A, B, V), ((WsHeader*)ws)->join_stamp);
   }
   return last_launch_status();
 }
 
+// after_count: the per-edge match counts come from the hg_join_count call
+// that last used this workspace on the same tables (checked on the device)
+// instead of a second intersection pass.
 template <typename K, typename Map>
 hg_status join_materialize_impl(const hg_config* cfg, const hg_table* A, const hg_table* B, int64_t* outA,
                                 int64_t* outB, uint64_t cap, int64_t* d_total, uint8_t* ws, cudaStream_t st,
-                                Map map) {
+                                Map map, bool after_count) {
   const uint64_t V = cfg->num_buckets, nA = A->n;
   JoinWs w = join_layout(ws, nA, V);
   WsHeader* hdr = (WsHeader*)ws;
   const int sms = dev_info().sms;
-  if (cudaMemsetAsync(w.moff, 0, (nA + 1) * 8, st) != cudaSuccess) return HG_ERR_CUDA;
-  if (nA > 0) {
-    const unsigned g = (unsigned)std::min<uint64_t>((nA + kJoinThreads - 1) / kJoinThreads, (uint64_t)sms * 16);
-    {
+  const unsigned g = (unsigned)std::min<uint64_t>(std::max<uint64_t>(1, (nA + kJoinThreads - 1) / kJoinThreads),
+                                                  (uint64_t)sms * 16);
+  if (after_count) {
+    HG_TRACE("k_join_check", st);
+    k_join_check<<<1, 1, 0, st>>>(join_stamp(A, B, V), hdr->join_stamp, &hdr->join_abort, &hdr->status, w.moff, nA);
+  } else {
+    if (cudaMemsetAsync(w.moff, 0, (nA + 1) * 8, st) != cudaSuccess) return HG_ERR_CUDA;
+    if (nA > 0) {
       HG_TRACE("k_join_elem", st);
       k_join_elem<K, Map><<<g, kJoinThreads, 0, st>>>(A->d_offsets, (const K*)A->d_keys, nA, B->d_offsets,
                                                       (const K*)B->d_keys, w.moff, nullptr, map);
     }
+  }
+  if (nA > 0) {
     hg_status rc = device_excl_scan<uint64_t>(w.moff, nA + 1, w.part, st);
     if (rc != HG_OK) return rc;
     {
       HG_TRACE("k_join_write", st);
       k_join_write<K, Map><<<g, kJoinThreads, 0, st>>>((const K*)A->d_keys, A->d_ids, nA, B->d_offsets,
-                                                       (const K*)B->d_keys, B->d_ids, w.moff, outA, outB, cap, map);
+                                                       (const K*)B->d_keys, B->d_ids, w.moff, outA, outB, cap,
+                                                       &hdr->join_abort, map);
     }
   }
   {
     HG_TRACE("k_join_finish", st);
-    k_join_finish<<<1, 1, 0, st>>>(w.moff, nA, cap, d_total, &hdr->status);
+    k_join_finish<<<1, 1, 0, st>>>(w.moff, nA, cap, d_total, &hdr->status, &hdr->join_abort, hdr->join_stamp);
   }
   return last_launch_status();
 }
@@ -252,7 +304,7 @@ hg_status join_materialize_impl(const hg_config* cfg, const hg_table* A, const h
   template hg_status join_count_impl<K, M>(const hg_config*, const hg_table*, const hg_table*, int64_t*,       \
                                            int64_t*, uint8_t*, cudaStream_t, M);                              \
   template hg_status join_materialize_impl<K, M>(const hg_config*, const hg_table*, const hg_table*, int64_t*, \
-                                                 int64_t*, uint64_t, int64_t*, uint8_t*, cudaStream_t, M);
+                                                 int64_t*, uint64_t, int64_t*, uint8_t*, cudaStream_t, M, bool);
 HG_INST(uint32_t, MurmurMap)
 HG_INST(uint64_t, MurmurMap)
 HG_INST(uint32_t, LearnedMap)

@@ -774,4 +774,39 @@ hg_status hg_bucket_stats(const hg_config* cfg, const void* d_keys, uint64_t n, 
   return last_launch_status();
 }
 
+size_t hg_learned_judge_workspace_size(void) { return (size_t)kLrnBlocks * 4 * 8 + 8 * 8; }
+
+// Murmur judges the learned map: bucket-length statistics of both maps over
+// the same keys (hg_bucket_stats twice, the learned map from cfg->d_model,
+// Murmur with cfg->seed), then the fallback rule on the host.
+hg_status hg_learned_judge(const hg_config* cfg, const void* d_keys, uint64_t n, double var_tolerance,
+                           double max_factor, uint32_t* d_counts, void* d_ws, size_t ws_bytes, double* h_stats8,
+                           int32_t* h_keep, void* stream) {
+  hg_status rc = validate_config(cfg);
+  if (rc != HG_OK) return rc;
+  if (cfg->map != HG_MAP_LEARNED || !h_keep || !d_ws) return HG_ERR_INVALID_ARG;
+  if (ws_bytes < hg_learned_judge_workspace_size()) return HG_ERR_WORKSPACE_TOO_SMALL;
+  if (!(var_tolerance > 0.0)) var_tolerance = HG_LEARNED_VAR_TOLERANCE;
+  if (!(max_factor > 0.0)) max_factor = HG_LEARNED_MAX_FACTOR;
+  const size_t part = (size_t)kLrnBlocks * 4 * 8;
+  double* d_out = (double*)((uint8_t*)d_ws + part);  // learned [0..3], Murmur [4..7]
+  hg_config mm = *cfg;
+  mm.map = HG_MAP_MURMUR3;
+  mm.d_model = nullptr;
+  rc = hg_bucket_stats(cfg, d_keys, n, d_counts, d_out, d_ws, part, stream);
+  if (rc != HG_OK) return rc;
+  rc = hg_bucket_stats(&mm, d_keys, n, d_counts, d_out + 4, d_ws, part, stream);
+  if (rc != HG_OK) return rc;
+  double st[8];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(st, d_out, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess) return HG_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HG_ERR_CUDA;
+  // kept while the learned map's bucket-length variance and longest bucket
+  // stay within the tolerances of Murmur's on the same keys
+  *h_keep = (st[2] <= var_tolerance * st[6] && st[0] <= max_factor * st[4]) ? 1 : 0;
+  if (h_stats8)
+    for (int i = 0; i < 8; ++i) h_stats8[i] = st[i];
+  return HG_OK;
+}
+
 }  // extern "C"

@@ -37,8 +37,9 @@ def sampled_reference(orc, keys: np.ndarray, V: int, seed: int, sample_buckets: 
     counts = np.bincount(b.astype(np.int64), minlength=V)
     offsets = np.zeros(V + 1, dtype=np.uint64)
     np.cumsum(counts, out=offsets[1:])
-    sel = np.isin(b, sample_buckets.astype(np.uint64))
-    pos = np.nonzero(sel)[0]
+    mark = np.zeros(V, dtype=bool)
+    mark[sample_buckets.astype(np.int64)] = True
+    pos = np.nonzero(mark[b.astype(np.int64)])[0]
     bsel = b[pos]
     order = np.argsort(bsel, kind="stable")
     pos, bsel = pos[order], bsel[order]

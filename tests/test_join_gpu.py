@@ -93,3 +93,38 @@ def test_join_materialize_long_pair_lists(hg, orc, V):
     pa, pb = hg.join_materialize(tA, tB, capacity=cap)
     ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V, cap=cap)
     assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
+
+
+def test_join_materialize_after_count_reuses_the_count(hg, orc):
+    """hg_join_materialize_after_count writes the same pairs as the
+    self-contained call from the per-edge counts hg_join_count left in the
+    workspace; the device refuses a workspace counted for other tables, and
+    a second call without a new count (the counts are consumed)."""
+    import torch
+    a = dg.zipf_keys_u64(80_000, 3000, 31)
+    b = dg.uniform_domain_keys_u64(70_000, 3000, 32)
+    V = 1 << 15
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V, seed=1)
+    ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V)
+    M = len(ra)
+    ws = torch.empty(hg.join_workspace_size(tA.cfg, len(a), len(b)), dtype=torch.uint8, device="cuda")
+    out_a = torch.full((M,), -7, dtype=torch.int64, device="cuda")
+    out_b = torch.full((M,), -7, dtype=torch.int64, device="cuda")
+    total = torch.empty(1, dtype=torch.int64, device="cuda")
+    hg.join_count_into(tA, tB, total, None, ws)
+    assert int(total.item()) == M
+    hg.join_materialize_into(tA, tB, out_a, out_b, total, ws, after_count=True)
+    assert hg.workspace_status(ws) == 0 and int(total.item()) == M
+    assert np.array_equal(to_np(out_a), ra) and np.array_equal(to_np(out_b), rb)
+    # consumed: a second call without a count is refused on the device
+    out_a.fill_(-7)
+    hg.join_materialize_into(tA, tB, out_a, out_b, total, ws, after_count=True)
+    assert hg.workspace_status(ws) == 1 and int(total.item()) == 0   # HG_ERR_INVALID_ARG
+    assert bool((out_a == -7).all())
+    # counted for (A, B), materialised for (B, A): refused
+    hg.join_count_into(tA, tB, total, None, ws)
+    hg.join_materialize_into(tB, tA, out_a, out_b, total, ws, after_count=True)
+    assert hg.workspace_status(ws) == 1
+    # the convenience call counts and then materialises from that count
+    pa, pb = hg.join_materialize(tA, tB)
+    assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
