@@ -1410,8 +1410,11 @@ __global__ void k_scatter_counts(const uint32_t* __restrict__ Qi, const uint32_t
 #endif
 constexpr int kUnpermuteThreads = 1024;
 constexpr uint32_t kUnpermuteTile = HG_UNPERMUTE_TILE;  // outputs per merge tile (shared memory: 4 B each)
-constexpr int kUnpermuteGPW = 8;  // groups per warp: 256 groups / 32 warps
 
+// Every warp merges the groups warp, warp + 32, ... (GPW of them); per round
+// it loads UNR runs of 32 (position, count) pairs of each of its groups, so
+// GPW * UNR pairs per lane are in flight (eight for any number of groups).
+template <int GPW, int UNR>
 __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t* __restrict__ Qi,
                                                                  const uint32_t* __restrict__ Qc,
                                                                  const uint32_t* __restrict__ GS, uint32_t ng,
@@ -1435,10 +1438,10 @@ __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t*
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint64_t o0 = ob; o0 < oe; o0 += kUnpermuteTile) {
     const uint64_t o1 = min(o0 + (uint64_t)kUnpermuteTile, oe);
-    uint32_t c[kUnpermuteGPW], e[kUnpermuteGPW];
-    bool act[kUnpermuteGPW];
+    uint32_t c[GPW], e[GPW];
+    bool act[GPW];
 #pragma unroll
-    for (int k = 0; k < kUnpermuteGPW; ++k) {
+    for (int k = 0; k < GPW; ++k) {
       const uint32_t g = warp + k * nw;
       act[k] = g < ng;
       c[k] = act[k] ? cur[g] : 0u;
@@ -1446,31 +1449,37 @@ __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t*
     }
     bool any = true;
     while (any) {
-      uint32_t v[kUnpermuteGPW], x[kUnpermuteGPW];
+      uint32_t v[GPW][UNR], x[GPW][UNR];
 #pragma unroll
-      for (int k = 0; k < kUnpermuteGPW; ++k) {
-        v[k] = 0xffffffffu;
-        x[k] = 0u;
-        const uint32_t j = c[k] + lane;
-        if (act[k] && j < e[k]) {
-          v[k] = __ldcs(Qi + j);
-          x[k] = __ldcs(Qc + j);
+      for (int k = 0; k < GPW; ++k) {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          v[k][u] = 0xffffffffu;
+          x[k][u] = 0u;
+          const uint32_t j = c[k] + 32u * u + lane;
+          if (act[k] && j < e[k]) {
+            v[k][u] = __ldcs(Qi + j);
+            x[k][u] = __ldcs(Qc + j);
+          }
         }
       }
       any = false;
 #pragma unroll
-      for (int k = 0; k < kUnpermuteGPW; ++k) {
-        if (!act[k]) continue;  // warp-uniform
-        const bool in = (uint64_t)v[k] < o1;
-        if (in) out_s[v[k] - (uint32_t)o0] = x[k];
-        const uint32_t n = __popc(__ballot_sync(kFull, in));
-        c[k] += n;
-        act[k] = n == 32;
+      for (int k = 0; k < GPW; ++k) {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          if (!act[k]) break;  // warp-uniform
+          const bool in = (uint64_t)v[k][u] < o1;
+          if (in) out_s[v[k][u] - (uint32_t)o0] = x[k][u];
+          const uint32_t n = __popc(__ballot_sync(kFull, in));
+          c[k] += n;
+          act[k] = n == 32;
+        }
         any |= act[k];
       }
     }
 #pragma unroll
-    for (int k = 0; k < kUnpermuteGPW; ++k) {
+    for (int k = 0; k < GPW; ++k) {
       const uint32_t g = warp + k * nw;
       if (g < ng && lane == 0) cur[g] = c[k];
     }
@@ -1600,9 +1609,15 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
       k_scatter_counts<<<(unsigned)std::min<uint64_t>((q + 255) / 256, (uint64_t)di.sms * 16), 256, 0, st>>>(
           qi, qc, q, counts);
     else {
-      set_smem_once(k_unpermute, (size_t)kUnpermuteTile * 4);
-      k_unpermute<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.ng, q, span,
-                                                                                         counts);
+      auto launch = [&](auto kern) {
+        set_smem_once(kern, (size_t)kUnpermuteTile * 4);
+        kern<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.ng, q, span,
+                                                                                    counts);
+      };
+      if (p.ng <= 32) launch(k_unpermute<1, 8>);
+      else if (p.ng <= 64) launch(k_unpermute<2, 4>);
+      else if (p.ng <= 128) launch(k_unpermute<4, 2>);
+      else launch(k_unpermute<8, 1>);
     }
   }
   return last_launch_status();

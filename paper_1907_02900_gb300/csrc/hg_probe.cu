@@ -7,9 +7,52 @@
 
 namespace hg {
 
-// Each thread probes QPT queries whose loads are issued together, so that
-// several independent random reads are in flight per thread.
-template <typename K, typename Map, int QPT>
+// Table loads: read-only path by default; HG_PROBE_LD = 1 caches them in L2
+// only, 2 reads them without allocating in L1 (variants for measurement).
+#ifndef HG_PROBE_LD
+#define HG_PROBE_LD 0
+#endif
+template <typename T>
+__device__ __forceinline__ T probe_ld(const T* p) {
+#if HG_PROBE_LD == 1
+  return __ldcg(p);
+#else
+  return __ldg(p);
+#endif
+}
+#if HG_PROBE_LD == 2
+template <>
+__device__ __forceinline__ uint4 probe_ld<uint4>(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+template <>
+__device__ __forceinline__ uint32_t probe_ld<uint32_t>(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+template <>
+__device__ __forceinline__ uint64_t probe_ld<uint64_t>(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+#endif
+
+// One query per thread.  The grid is one wave of resident CTAs that sweeps
+// the queries in order (query base + threadIdx.x at sweep k, base =
+// (k * gridDim.x + blockIdx.x) * blockDim.x), so with grouped queries all
+// CTAs work inside one or two groups at any time and each group's slice of
+// the table stays in L2 while it is needed: the table is read from DRAM
+// once.  (A grid of two waves sweeps every group twice and reads the table
+// twice.)  Each thread loads its next query one sweep ahead, so the query's
+// DRAM latency is not on its chain of dependent loads.  The kernel is bound
+// by L1 request throughput: a warp's random loads touch 32 sectors each.
+template <typename K, typename Map>
 __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q, uint64_t nq,
                                                          const uint32_t* __restrict__ off,
                                                          const K* __restrict__ ck,
@@ -17,65 +60,40 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
                                                          const uint32_t* __restrict__ qpos, Map map) {
   map.init();
   const uint64_t bd = blockDim.x;
-  const uint64_t span = (uint64_t)gridDim.x * bd * QPT;
-  for (uint64_t base = (uint64_t)blockIdx.x * bd * QPT + threadIdx.x; base < nq; base += span) {
-    K key[QPT];
-    uint32_t s[QPT], e[QPT], c[QPT];
-#pragma unroll
-    for (int k = 0; k < QPT; ++k) {
-      const uint64_t i = base + k * bd;
-      key[k] = i < nq ? __ldcs(q + i) : K(0);
-    }
+  const uint64_t span = (uint64_t)gridDim.x * bd;
+  uint64_t base = (uint64_t)blockIdx.x * bd;
+  K next = base + threadIdx.x < nq ? __ldcs(q + base + threadIdx.x) : K(0);
+  for (; base < nq; base += span) {
+    const uint64_t i = base + threadIdx.x;
+    const K key = next;
+    next = i + span < nq ? __ldcs(q + i + span) : K(0);
+    if (i >= nq) continue;
     // The two offsets of a bucket come from one aligned 16-byte load (a random
-    // DRAM access costs a whole burst, so one request beats two); only a
-    // bucket in the last slot of its quad needs a second load.
-    uint32_t bq[QPT];
-    uint4 o4[QPT];
-#pragma unroll
-    for (int k = 0; k < QPT; ++k) {
-      const uint64_t i = base + k * bd;
-      bq[k] = i < nq ? map(key[k], qpos ? __ldg(qpos + i) : (uint32_t)i) : 0u;
-      if ((bq[k] >> 2) < nquads) {
-        o4[k] = __ldg(reinterpret_cast<const uint4*>(off) + (bq[k] >> 2));
-      } else {  // quad not wholly inside the offsets array (or array not 16-byte aligned)
-        o4[k] = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t r = bq[k] & 3u;
-        const uint32_t lo = __ldg(off + bq[k]), hi = __ldg(off + bq[k] + 1);
-        if (r == 0) { o4[k].x = lo; o4[k].y = hi; }
-        else if (r == 1) { o4[k].y = lo; o4[k].z = hi; }
-        else if (r == 2) { o4[k].z = lo; o4[k].w = hi; }
-        else { o4[k].w = lo; }
-      }
+    // access costs a whole sector either way, so one request beats two); only
+    // a bucket in the last slot of its quad needs a second load.
+    const uint32_t b = map(key, qpos ? __ldg(qpos + i) : (uint32_t)i);
+    const uint32_t r = b & 3u;
+    uint32_t s, e;
+    if ((b >> 2) < nquads) {
+      const uint4 o4 = probe_ld(reinterpret_cast<const uint4*>(off) + (b >> 2));
+      s = r == 0 ? o4.x : r == 1 ? o4.y : r == 2 ? o4.z : o4.w;
+      e = r == 0 ? o4.y : r == 1 ? o4.z : r == 2 ? o4.w : probe_ld(off + b + 1);
+    } else {  // quad not wholly inside the offsets array (or array not 16-byte aligned)
+      s = probe_ld(off + b);
+      e = probe_ld(off + b + 1);
     }
-#pragma unroll
-    for (int k = 0; k < QPT; ++k) {
-      const uint64_t i = base + k * bd;
-      const uint32_t r = bq[k] & 3u;
-      const uint32_t lo = r == 0 ? o4[k].x : r == 1 ? o4[k].y : r == 2 ? o4[k].z : o4[k].w;
-      const uint32_t hi = r == 0 ? o4[k].y : r == 1 ? o4[k].z : r == 2 ? o4[k].w : __ldg(off + bq[k] + 1);
-      s[k] = i < nq ? lo : 0u;
-      e[k] = i < nq ? hi : 0u;
-    }
-    K first[QPT];
-#pragma unroll
-    for (int k = 0; k < QPT; ++k) first[k] = s[k] < e[k] ? __ldg(ck + s[k]) : K(0);
-#pragma unroll
-    for (int k = 0; k < QPT; ++k) {
-      uint32_t cnt = (s[k] < e[k] && first[k] == key[k]) ? 1u : 0u;
-      uint32_t j = s[k] + 1;
+    uint32_t cnt = 0;
+    if (s < e) {
+      cnt = probe_ld(ck + s) == key;
+      uint32_t j = s + 1;
       // four independent loads in flight per round for long buckets
-      for (; j + 4 <= e[k]; j += 4) {
-        const K a0 = __ldg(ck + j), a1 = __ldg(ck + j + 1), a2 = __ldg(ck + j + 2), a3 = __ldg(ck + j + 3);
-        cnt += (a0 == key[k]) + (a1 == key[k]) + (a2 == key[k]) + (a3 == key[k]);
+      for (; j + 4 <= e; j += 4) {
+        const K a0 = probe_ld(ck + j), a1 = probe_ld(ck + j + 1), a2 = probe_ld(ck + j + 2), a3 = probe_ld(ck + j + 3);
+        cnt += (a0 == key) + (a1 == key) + (a2 == key) + (a3 == key);
       }
-      for (; j < e[k]; ++j) cnt += __ldg(ck + j) == key[k];
-      c[k] = cnt;
+      for (; j < e; ++j) cnt += probe_ld(ck + j) == key;
     }
-#pragma unroll
-    for (int k = 0; k < QPT; ++k) {
-      const uint64_t i = base + k * bd;
-      if (i < nq) __stcs(out + i, c[k]);
-    }
+    __stcs(out + i, cnt);
   }
 }
 
@@ -86,12 +104,18 @@ hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck
   // quads of offsets wholly inside the V+1 entries (none if not 16-byte aligned)
   const uint32_t nquads = ((uintptr_t)off % 16 == 0) ? (uint32_t)((V + 1) / 4) : 0u;
   const int sms = dev_info().sms;
-  const uint64_t per_block = (uint64_t)kProbeThreads * kProbeQPT;
-  const uint64_t want = (nq + per_block - 1) / per_block;
-  const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)sms * 16);
+  auto kern = k_probe<K, Map>;
+  static int per_sm = 0;  // resident CTAs per SM of this instantiation
+  if (per_sm == 0) {
+    int x = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, kern, kProbeThreads, 0) != cudaSuccess || x <= 0) x = 4;
+    per_sm = x;
+  }
+  const uint64_t want = (nq + kProbeThreads - 1) / kProbeThreads;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * per_sm));
   {
     HG_TRACE("k_probe", st);
-    k_probe<K, Map, kProbeQPT><<<grid, kProbeThreads, 0, st>>>(q, nq, off, ck, out, nquads, qpos, map);
+    kern<<<grid, kProbeThreads, 0, st>>>(q, nq, off, ck, out, nquads, qpos, map);
   }
   return last_launch_status();
 }

@@ -11,11 +11,7 @@ namespace hg {
 #ifndef HG_PROBE_THREADS
 #define HG_PROBE_THREADS 256
 #endif
-#ifndef HG_PROBE_QPT
-#define HG_PROBE_QPT 1
-#endif
 constexpr int kProbeThreads = HG_PROBE_THREADS;
-constexpr int kProbeQPT = HG_PROBE_QPT;  // queries per thread with their loads in flight together
 
 // qpos (optional): input position of each query, for maps that need it
 // (queries probed in a permuted order); null means query i is at position i.
