@@ -407,13 +407,20 @@ def run_scale(c: Ctx):
     V = 1 << log2v
     q = n
     seed = dg.SEED_SCALE + 1000 * c.rank
-    keys_h = dg.dup_keys_u32(n, args.dup, seed) if args.dup > 0 else dg.uniform_keys_u32(n, seed)
-    q_h = dg.queries_u32(q, keys_h, args.hit, seed + 1)
-    keys_p = torch.from_numpy(keys_h.view(np.int32)).pin_memory()
-    q_p = torch.from_numpy(q_h.view(np.int32)).pin_memory()
-    del keys_h, q_h
-    keys_d = keys_p.to(c.dev).view(torch.uint32)
-    q_d = q_p.to(c.dev).view(torch.uint32)
+    import paper_1907_02900_gb300.datagen_gpu as dgg
+    if args.dup > 0:
+        keys_h = dg.dup_keys_u32(n, args.dup, seed)
+        keys_d = torch.from_numpy(keys_h.view(np.int32)).to(c.dev).view(torch.uint32)
+        del keys_h
+    else:   # the same numbers as datagen.uniform_keys_u32, drawn on the device
+        keys_d = dgg.uniform_keys_u32(n, seed, device=c.dev)
+    q_d = dgg.queries_u32(q, keys_d, args.hit, seed + 1)
+    # pinned host copies for the end-to-end leg
+    keys_p = torch.empty(n, dtype=torch.int32, pin_memory=True) if args.e2e_steps > 0 else None
+    q_p = torch.empty(q, dtype=torch.int32, pin_memory=True) if args.e2e_steps > 0 else None
+    if keys_p is not None:
+        keys_p.copy_(keys_d.view(torch.int32))
+        q_p.copy_(q_d.view(torch.int32))
     cfg = hg.make_config(hg.KEY_U32, V, 0, args.algo)
     ids_d = None
     if args.explicit_ids:   # a permutation-like id array: ids = position * odd constant (mod 2^32)

@@ -9,6 +9,7 @@ this package.
 Functions and the paper passage each follows:
   murmur3_x86_32      Section 2 "Hashing" (Eq. 1 names Murmur hashing)
   buckets             Eq. 1, hash(a) mod V; or the learned map (not in the paper)
+  bucket_counts       the bucket histogram the build's prefix sum turns into offsets
   build               Alg. 1 / Alg. 2 / Section 3.1: CSR with V+1 offsets and
                       N (key, id) edges, grouped by bucket; canonical order
                       inside a bucket = ascending input position
@@ -68,6 +69,8 @@ def lib():
         L.orc_hash_keys.argtypes = [i32, vp, u64, u32, vp]
         L.orc_bucket_keys.restype = i32
         L.orc_bucket_keys.argtypes = [i32, vp, u64, i32, u32, u64, vp, vp]
+        L.orc_bucket_counts.restype = i32
+        L.orc_bucket_counts.argtypes = [i32, vp, u64, i32, u32, u64, vp, vp]
         L.orc_build.restype = i32
         L.orc_build.argtypes = [i32, vp, vp, u64, i32, u32, u64, vp, vp, vp, vp]
         L.orc_probe.restype = i32
@@ -114,6 +117,18 @@ def buckets(keys: np.ndarray, V: int, seed: int = 0, model: np.ndarray | None = 
     kind = MAP_LEARNED if model is not None else MAP_MURMUR3
     rc = lib().orc_bucket_keys(_key_type(keys), _ptr(keys), len(keys), kind, seed & 0xFFFFFFFF, V,
                                _ptr(model), _ptr(out))
+    if rc:
+        raise ValueError("invalid bucket map")
+    return out
+
+
+def bucket_counts(keys: np.ndarray, V: int, seed: int = 0, model: np.ndarray | None = None) -> np.ndarray:
+    """uint32[V]: number of keys in each bucket (the histogram under the CSR offsets)."""
+    keys = np.ascontiguousarray(keys)
+    out = np.empty(V, dtype=np.uint32)
+    kind = MAP_LEARNED if model is not None else MAP_MURMUR3
+    rc = lib().orc_bucket_counts(_key_type(keys), _ptr(keys), len(keys), kind, seed & 0xFFFFFFFF, V, _ptr(model),
+                                 _ptr(out))
     if rc:
         raise ValueError("invalid bucket map")
     return out

@@ -208,6 +208,18 @@ int orc_bucket_keys(int key_type, const void* keys, uint64_t n, int map_kind, ui
   return 0;
 }
 
+// Number of keys in every bucket (the histogram the build's prefix sum turns
+// into the CSR offsets, Alg. 1 and Section 3.1), for key sets too large to
+// keep one bucket per key in memory.  counts: V entries, overwritten.
+int orc_bucket_counts(int key_type, const void* keys, uint64_t n, int map_kind, uint32_t seed, uint64_t V,
+                      const void* model, uint32_t* counts) {
+  Map mp;
+  if (!make_map(map_kind, seed, V, model, mp)) return 1;
+  for (uint64_t v = 0; v < V; ++v) counts[v] = 0;
+  for (uint64_t i = 0; i < n; ++i) ++counts[bucket_of(mp, key_type, key_at(key_type, keys, i))];
+  return 0;
+}
+
 // HashGraph build (Alg. 1 / Alg. 2 define the same table): the table is the
 // input grouped by bucket.  Definition used here: sort input positions by
 // (bucket, position); offsets[v] = number of keys whose bucket is below v.

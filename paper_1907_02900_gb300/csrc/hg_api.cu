@@ -48,18 +48,34 @@ hg_status validate_config(const hg_config* cfg) {
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-// Which algorithm a build uses, and the V2 plan when it is V2.
-static hg_status choose_algo(const hg_config* cfg, uint64_t n, bool* use_v2, Plan* plan) {
+// Which algorithm a build uses: V1 (Alg. 1), V2 (Alg. 2, one two-level
+// plan) or V2 with one more relabeling level (slabs, when one two-level plan
+// would leave its bins larger than shared memory); and the plan.
+enum BuildKind { kBuildV1, kBuildV2, kBuildSlabs };
+static hg_status choose_algo(const hg_config* cfg, uint64_t n, BuildKind* kind, Plan* plan, SlabPlan* slabs) {
+  if (cfg->algo == HG_ALGO_V1) {
+    *kind = kBuildV1;
+    return HG_OK;
+  }
   const bool v2ok = make_plan_v2(cfg, n, plan);
-  if (cfg->algo == HG_ALGO_V2) {
-    if (!v2ok) return HG_ERR_UNSUPPORTED;
-    *use_v2 = true;
-  } else if (cfg->algo == HG_ALGO_V1) {
-    *use_v2 = false;
+  if (v2ok && (cfg->bin_shift != 0 || v2_plan_fits(*plan))) {
+    *kind = kBuildV2;
+  } else if (make_slab_plan(cfg, n, slabs)) {
+    *kind = kBuildSlabs;
+  } else if (v2ok) {
+    *kind = kBuildV2;  // bins larger than shared memory go to the oversized-bin kernels
+  } else if (cfg->algo == HG_ALGO_V2) {
+    return HG_ERR_UNSUPPORTED;
   } else {
-    *use_v2 = v2ok;
+    *kind = kBuildV1;
   }
   return HG_OK;
+}
+
+static size_t build_ws_bytes(const hg_config* cfg, uint64_t n, BuildKind kind, const Plan& p, const SlabPlan& sp) {
+  if (kind == kBuildV2) return p.total;
+  if (kind == kBuildSlabs) return sp.total;
+  return v1_workspace_bytes(cfg->key_type == HG_KEY_U64 ? 8 : 4, n, cfg->num_buckets);
 }
 
 }  // namespace hg
@@ -86,11 +102,11 @@ const char* hg_status_string(hg_status s) {
 
 size_t hg_build_workspace_size(const hg_config* cfg, uint64_t n) {
   if (validate_config(cfg) != HG_OK) return 0;
-  bool v2 = false;
+  BuildKind kind = kBuildV1;
   Plan p{};
-  if (choose_algo(cfg, n, &v2, &p) != HG_OK) return 0;
-  if (v2) return p.total;
-  return v1_workspace_bytes(cfg->key_type == HG_KEY_U64 ? 8 : 4, n, cfg->num_buckets);
+  SlabPlan sp{};
+  if (choose_algo(cfg, n, &kind, &p, &sp) != HG_OK) return 0;
+  return build_ws_bytes(cfg, n, kind, p, sp);
 }
 
 hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids, uint64_t n,
@@ -104,12 +120,12 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_i
   if (!aligned(d_keys, 16) || !aligned(d_ids, 16) || !aligned(d_csr_keys, 16) || !aligned(d_csr_ids, 16) ||
       !aligned(d_offsets, 4) || !aligned(d_ws, 256))
     return HG_ERR_INVALID_ARG;
-  bool v2 = false;
+  BuildKind kind = kBuildV1;
   Plan p{};
-  rc = choose_algo(cfg, n, &v2, &p);
+  SlabPlan sp{};
+  rc = choose_algo(cfg, n, &kind, &p, &sp);
   if (rc != HG_OK) return rc;
-  const size_t need = v2 ? p.total : v1_workspace_bytes(cfg->key_type == HG_KEY_U64 ? 8 : 4, n, cfg->num_buckets);
-  if (ws_bytes < need) return HG_ERR_WORKSPACE_TOO_SMALL;
+  if (ws_bytes < build_ws_bytes(cfg, n, kind, p, sp)) return HG_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
   if (n == 0) {
@@ -118,8 +134,11 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_i
   }
   return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
     using K = decltype(k);
-    if (v2)
+    if (kind == kBuildV2)
       return build_v2<K>(p, (const K*)d_keys, d_ids, d_offsets, (K*)d_csr_keys, d_csr_ids, (uint8_t*)d_ws, st, map);
+    if (kind == kBuildSlabs)
+      return build_slabs<K>(cfg, sp, (const K*)d_keys, d_ids, d_offsets, (K*)d_csr_keys, d_csr_ids, (uint8_t*)d_ws,
+                            st, map);
     return build_v1<K>(n, cfg->num_buckets, (const K*)d_keys, d_ids, d_offsets, (K*)d_csr_keys, d_csr_ids,
                        (uint8_t*)d_ws, st, map);
   });

@@ -1139,7 +1139,8 @@ static void set_smem_once(F* kernel, size_t bytes) {
 
 template <typename K, typename Map>
 hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
-                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map, uint32_t pos_base) {
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map, uint32_t pos_base,
+                   bool positional_ids) {
   WsHeader* hdr = (WsHeader*)ws;
   uint32_t* status = &hdr->status;
   uint32_t* H = (uint32_t*)(ws + p.o_H);
@@ -1178,7 +1179,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   // shared-memory bin build, the partitions may rank tiles in any order.
   // Both variants of each such kernel are launched; the one that does not
   // match the order mode returns at once.
-  const bool any_order = ids == nullptr;
+  const bool any_order = ids == nullptr || positional_ids;
   {
     HG_TRACE("k_scan_bins", st);
     HugeArgs h{};
@@ -1225,9 +1226,14 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
       kern<<<p.G, kPartNW * 32, own + x.stage_bytes, st>>>(x, map);
     };
     HG_TRACE("k_partition_A", st);
-    if (any_order)
+    // (a tile of carried ids takes the stable variant's tile size: the
+    // larger one leaves no room for staging the ids)
+    if (any_order && ids == nullptr)
       launch(k_partition<K, Map, false, part_ipt_keys<K, true>(), kPartNW, part_minb_keys<K, true>(), true>,
              part_ipt_keys<K, true>());
+    else if (any_order)
+      launch(k_partition<K, Map, false, part_ipt_keys<K, false>(), kPartNW, part_minb_keys<K, false>(), true>,
+             part_ipt_keys<K, false>());
     launch(k_partition<K, Map, false, part_ipt_keys<K, false>(), kPartNW, part_minb_keys<K, false>(), false>,
            part_ipt_keys<K, false>());
   }
@@ -1324,6 +1330,152 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     auto kx = k_huge_scatter<K, Map>;
     set_smem_once(kx, sm);
     kx<<<grid, kBinNW * 32, sm, st>>>(ba, hrows, rowdesc, rowcnt, map);
+  }
+  return last_launch_status();
+}
+
+bool v2_plan_fits(const Plan& p) {
+  if (p.n == 0) return true;
+  const double mean = (double)p.n * (double)(1ull << p.s) / (double)p.V;
+  return mean + 5.0 * std::sqrt(mean) + 16.0 <= (double)p.emax;
+}
+
+bool make_slab_plan(const hg_config* cfg, uint64_t n, SlabPlan* p) {
+  if (cfg->bin_shift != 0 || n == 0) return false;  // an explicit bin size asks for one two-level plan
+  const DevInfo& di = dev_info();
+  p->kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  p->n = n;
+  p->V = cfg->num_buckets;
+  const double emax = p->kb == 4 ? kBinEmaxU32 : kBinEmaxU64;
+  const double alpha = (double)n / (double)p->V;
+  // largest bins (2^s buckets) that still fit shared memory at this load
+  int s_fit = -1;
+  for (int s = 0; s <= (int)kMaxBinShift; ++s) {
+    const double mean = alpha * (double)(1ull << s);
+    if (mean + 5.0 * std::sqrt(mean) + 16.0 <= emax) s_fit = s;
+  }
+  if (s_fit < 0) return false;  // a bin of one bucket would overflow: no relabeling helps
+  p->Ls = (uint32_t)s_fit + kMaxBinsLog2;
+  const uint64_t S = (p->V + (1ull << p->Ls) - 1) >> p->Ls;
+  if (S < 2 || S > 256) return false;
+  p->S = (uint32_t)S;
+  const int sms = std::max(di.sms, 1);
+  uint64_t chunk = std::max<uint64_t>(kPartTile, (n + 2 * sms - 1) / (2 * sms));
+  chunk = (chunk + 15) / 16 * 16;
+  p->chunk = chunk;
+  p->G = (uint32_t)std::max<uint64_t>(1, (n + chunk - 1) / chunk);
+  hg_config cs = *cfg;
+  cs.num_buckets = std::min<uint64_t>(1ull << p->Ls, p->V);
+  cs.bin_shift = 0;
+  if (!make_plan_v2(&cs, n, &p->sub)) return false;
+  size_t o = sizeof(WsHeader);
+  p->o_H = o;   o = align_up(o + (size_t)p->G * p->S * 4);
+  p->o_C = o;   o = align_up(o + (size_t)p->G * p->S * 4);
+  p->o_CT = o;  o = align_up(o + (size_t)p->S * 4);
+  p->o_T = o;   o = align_up(o + (size_t)p->S * 4);
+  p->o_BS = o;  o = align_up(o + ((size_t)p->S + 1) * 4);
+  p->o_ovf = o; o = align_up(o + (size_t)p->S * 4 + 16);
+  p->o_k = o;   o = align_up(o + ((size_t)n + 16) * p->kb);
+  p->o_i = o;   o = align_up(o + ((size_t)n + 16) * 4);
+  p->o_sub = o; o = align_up(o + p->sub.total);
+  p->total = o;
+  return true;
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ a, uint64_t n, uint32_t v) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    a[i] = v;
+}
+
+// A slab build records its device errors in its own workspace header; they
+// are carried over to the caller's.
+__global__ void k_carry_status(const uint32_t* __restrict__ from, uint32_t* to) {
+  if (*from) set_status(to, *from);
+}
+
+template <typename K, typename Map>
+hg_status build_slabs(const hg_config* cfg, const SlabPlan& p, const K* keys, const uint32_t* ids,
+                      uint32_t* offsets, K* csr_k, uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map) {
+  WsHeader* hdr = (WsHeader*)ws;
+  uint32_t* H = (uint32_t*)(ws + p.o_H);
+  uint32_t* C = (uint32_t*)(ws + p.o_C);
+  uint32_t* CT = (uint32_t*)(ws + p.o_CT);
+  uint32_t* T = (uint32_t*)(ws + p.o_T);
+  uint32_t* BS = (uint32_t*)(ws + p.o_BS);
+  uint32_t* ovf = (uint32_t*)(ws + p.o_ovf);
+  K* lk = (K*)(ws + p.o_k);
+  uint32_t* li = (uint32_t*)(ws + p.o_i);
+  uint8_t* sub = ws + p.o_sub;
+  const DevInfo& di = dev_info();
+  // 1. slab of every key (bucket >> Ls), counted per input chunk
+  {
+    const size_t sm = hist_stage_offset(p.S) + Map::kStageBytes;
+    auto kern = k_hist<K, Map>;
+    set_smem_once(kern, sm);
+    HG_TRACE("k_hist_slab", st);
+    kern<<<p.G, kHistThreads, sm, st>>>(keys, p.n, p.chunk, p.Ls, p.S, 0, p.S, H, C, map,
+                                        (uint32_t)Map::kStageBytes);
+    k_colscan<<<1, 256, 0, st>>>(H, p.G, p.S, T);
+    k_colscan<<<1, 256, 0, st>>>(C, p.G, p.S, CT);
+    k_scan_bins<<<1, 1024, 0, st>>>(T, p.S, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.S, 0, (uint32_t)p.n,
+                                    HugeArgs{}, nullptr);
+  }
+  // 2. stable partition by slab: each slab keeps its keys in input order,
+  //    with their ids (the input positions when none are given)
+  {
+    PartArgs<K> pa{};
+    pa.in_k = keys;
+    pa.in_i = ids;
+    pa.out_k = lk;
+    pa.out_i = li;
+    pa.n = p.n;
+    pa.chunk = p.chunk;
+    pa.G = p.G;
+    pa.s = p.Ls;
+    pa.sshift = 0;
+    pa.nbins = p.S;
+    pa.nsb = p.S;
+    pa.H = H;
+    pa.C = C;
+    pa.CT = CT;
+    pa.BS = BS;
+    pa.status = &hdr->status;
+    pa.order = nullptr;
+    constexpr int ipt = part_ipt_keys<K, false>();
+    auto kern = k_partition<K, Map, false, ipt, kPartNW, part_minb_keys<K, false>(), false>;
+    const size_t own = part_smem_bytes(sizeof(K), ids != nullptr, ipt, false, kPartNW);
+    pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
+    set_smem_once(kern, own + pa.stage_bytes);
+    HG_TRACE("k_partition_slab", st);
+    kern<<<p.G, kPartNW * 32, own + pa.stage_bytes, st>>>(pa, map);
+  }
+  // 3. slab sizes to the host, then one two-level build per slab
+  uint32_t hT[256];
+  if (cudaMemcpyAsync(hT, T, (size_t)p.S * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HG_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HG_ERR_CUDA;
+  uint64_t start = 0;
+  for (uint32_t sl = 0; sl < p.S; ++sl) {
+    const uint64_t b0 = (uint64_t)sl << p.Ls;
+    const uint64_t Vs = std::min<uint64_t>(1ull << p.Ls, p.V - b0);
+    const uint64_t ns = hT[sl];
+    if (ns == 0) {
+      k_fill_u32<<<(unsigned)std::min<uint64_t>((Vs + 256) / 256, (uint64_t)di.sms * 8), 256, 0, st>>>(
+          offsets + b0, Vs + 1, (uint32_t)start);
+      continue;
+    }
+    hg_config cs = *cfg;
+    cs.num_buckets = Vs;
+    cs.bin_shift = 0;
+    Plan ps{};
+    if (!make_plan_v2(&cs, ns, &ps) || ps.total > p.sub.total) return HG_ERR_UNSUPPORTED;
+    Map ms = map;
+    ms.slab_base = (uint32_t)b0;
+    if (cudaMemsetAsync(sub, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+    hg_status rc = build_v2<K, Map>(ps, lk + start, li + start, offsets + b0, csr_k + start, csr_i + start, sub, st,
+                                    ms, (uint32_t)start, ids == nullptr);
+    if (rc != HG_OK) return rc;
+    k_carry_status<<<1, 1, 0, st>>>(&((WsHeader*)sub)->status, &hdr->status);
+    start += ns;
   }
   return last_launch_status();
 }
@@ -1731,7 +1883,9 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
 // Explicit instantiations used by hg_api.cu (build entry point).
 #define HG_INST(K, M)                                                                                   \
   template hg_status build_v2<K, M>(const Plan&, const K*, const uint32_t*, uint32_t*, K*, uint32_t*, \
-                                    uint8_t*, cudaStream_t, M, uint32_t);                               \
+                                    uint8_t*, cudaStream_t, M, uint32_t, bool);                         \
+  template hg_status build_slabs<K, M>(const hg_config*, const SlabPlan&, const K*, const uint32_t*,  \
+                                       uint32_t*, K*, uint32_t*, uint8_t*, cudaStream_t, M);            \
   template hg_status build_v1<K, M>(uint64_t, uint64_t, const K*, const uint32_t*, uint32_t*, K*,       \
                                     uint32_t*, uint8_t*, cudaStream_t, M);                              \
   template hg_status probe_binned_impl<K, M>(const ProbePlan&, uint64_t, const hg_table*, const K*,     \
@@ -1744,7 +1898,7 @@ HG_INST(uint64_t, LearnedMap)
 // batched tables: V2 build and binned probe only (the map needs positions)
 template hg_status build_v2<uint32_t, BatchedMap>(const Plan&, const uint32_t*, const uint32_t*, uint32_t*,
                                                   uint32_t*, uint32_t*, uint8_t*, cudaStream_t, BatchedMap,
-                                                  uint32_t);
+                                                  uint32_t, bool);
 template hg_status probe_binned_impl<uint32_t, BatchedMap>(const ProbePlan&, uint64_t, const hg_table*,
                                                            const uint32_t*, uint64_t, uint32_t*, uint8_t*,
                                                            cudaStream_t, BatchedMap);

@@ -110,6 +110,27 @@ struct Plan {
 };
 
 bool make_plan_v2(const hg_config* cfg, uint64_t n, Plan* p);
+// Whether every bin of a uniform spread of the keys is expected to fit the
+// shared-memory bin build (mean + 5 standard deviations of a Poisson count).
+bool v2_plan_fits(const Plan& p);
+
+// Builds whose buckets need more than 2^15 bins of shared-memory size relabel
+// once more (Section 3.3, "Larger Inputs"): a stable partition of the keys by
+// slab of 2^Ls buckets, then one two-level build (Alg. 2) per slab into its
+// slice of the table.  The slab sizes are read back to the host between the
+// two steps (one stream synchronisation).
+struct SlabPlan {
+  int kb;
+  uint64_t n, V;
+  uint32_t Ls, S, G;
+  uint64_t chunk;
+  Plan sub;  // plan of a slab holding all n keys: the bound of every slab build's workspace
+  size_t o_H, o_C, o_CT, o_T, o_BS, o_ovf, o_k, o_i, o_sub, total;
+};
+bool make_slab_plan(const hg_config* cfg, uint64_t n, SlabPlan* p);
+template <typename K, typename Map>
+hg_status build_slabs(const hg_config* cfg, const SlabPlan& p, const K* keys, const uint32_t* ids,
+                      uint32_t* offsets, K* csr_k, uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map);
 
 // Binned probe: query groups by bucket range, workspace layout.
 struct ProbePlan {
@@ -129,9 +150,13 @@ size_t v1_workspace_bytes(int kb, uint64_t n, uint64_t V);
 
 // pos_base is added to every CSR offset written (the position of element 0
 // of these CSR arrays inside larger ones; 0 for a standalone table).
+// positional_ids: the ids carried are distinct input positions, in input
+// order (a slab of a larger build), so the partitions may rank tiles in any
+// order, as with implicit ids.
 template <typename K, typename Map>
 hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* offsets, K* csr_k,
-                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map, uint32_t pos_base = 0);
+                   uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map, uint32_t pos_base = 0,
+                   bool positional_ids = false);
 template <typename K, typename Map>
 hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, uint32_t* offsets,
                    K* csr_k, uint32_t* csr_i, uint8_t* ws, cudaStream_t st, Map map);

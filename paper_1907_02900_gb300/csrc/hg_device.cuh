@@ -65,16 +65,19 @@ struct FastMod {
 // key's table from it); out_id(pos) is the id stored for the element whose
 // carried id is pos (plain maps store it unchanged).
 // Eq. 1: bucket = hash(key) mod V.
+// slab_base: first bucket of the slab a build works on (the map returns the
+// bucket minus slab_base; 0 for a whole table).
 struct MurmurMap {
   static constexpr bool kNeedsPos = false;
   static constexpr size_t kStageBytes = 0;  // shared memory stage() can use
   uint32_t seed;
+  uint32_t slab_base;
   FastMod mod;
   __device__ __forceinline__ void init() {}
   __device__ __forceinline__ void stage(uint8_t*, size_t) {}
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t /*pos*/ = 0) const {
-    return mod(murmur3(key, seed));
+    return mod(murmur3(key, seed)) - slab_base;
   }
   __device__ __forceinline__ uint32_t out_id(uint32_t id) const { return id; }
 };
@@ -162,6 +165,7 @@ struct LearnedMap {
   static constexpr size_t kStageBytes = kStageLeaves * sizeof(LearnedLeaf);
   const uint8_t* blob;  // device pointer
   uint64_t Vcap;        // buckets of the table being built (host-provided bound)
+  uint32_t slab_base;   // first bucket of the slab being built (subtracted from the result)
   float a, b, Lf;
   uint32_t L;
   uint64_t V, vmax;
@@ -227,7 +231,7 @@ struct LearnedMap {
       else local = min((uint32_t)p, width - 1);
     }
     const uint64_t bk = (uint64_t)base + local;
-    return (uint32_t)(bk < vmax ? bk : vmax - 1);
+    return (uint32_t)(bk < vmax ? bk : vmax - 1) - slab_base;
   }
 };
 

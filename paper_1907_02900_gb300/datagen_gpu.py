@@ -54,3 +54,44 @@ def fill_batch(plan, bufs: dict, key_seed: int, query_seed: int, hit_rate: float
     if rc != 0:
         raise RuntimeError(f"hgd_batched_queries_u32: CUDA error {rc}")
     torch.cuda.current_stream().synchronize()
+
+
+def _one_table(n: int, dev):
+    """Layout arrays of a batch of one table of n entries: first positions
+    (uint64[2], padded = unpadded) and its length (uint32[1])."""
+    import torch
+    beg = torch.from_numpy(np.array([0, n], dtype=np.uint64).view(np.int64)).to(dev)
+    ln = torch.from_numpy(np.array([n], dtype=np.uint32).view(np.int32)).to(dev)
+    return beg, ln
+
+
+def uniform_keys_u32(n: int, seed: int, device="cuda", stream=None):
+    """datagen.uniform_keys_u32(n, seed) drawn on the device (CUDA uint32 tensor)."""
+    import torch
+    assert 0 <= n < (1 << 32)
+    out = torch.empty(n + 4, dtype=torch.uint32, device=device)[:n]
+    beg, ln = _one_table(n, out.device)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = load().hgd_batched_keys_u32(seed, 1, beg.data_ptr(), beg.data_ptr(), ln.data_ptr(), n, out.data_ptr(), st)
+    if rc != 0:
+        raise RuntimeError(f"hgd_batched_keys_u32: CUDA error {rc}")
+    torch.cuda.current_stream().synchronize()
+    return out
+
+
+def queries_u32(q: int, keys, hit_rate: float, seed: int, stream=None):
+    """datagen.queries_u32(q, keys, hit_rate, seed) drawn on the device from
+    the device key tensor (CUDA uint32 tensor)."""
+    import torch
+    n = keys.numel()
+    assert 0 <= q < (1 << 32) and n < (1 << 32)
+    out = torch.empty(q + 4, dtype=torch.uint32, device=keys.device)[:q]
+    qbeg, qln = _one_table(q, keys.device)
+    kbeg, kln = _one_table(n, keys.device)
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    rc = load().hgd_batched_queries_u32(seed, hit_rate, 1, qbeg.data_ptr(), qbeg.data_ptr(), qln.data_ptr(),
+                                        kbeg.data_ptr(), kln.data_ptr(), keys.data_ptr(), q, out.data_ptr(), st)
+    if rc != 0:
+        raise RuntimeError(f"hgd_batched_queries_u32: CUDA error {rc}")
+    torch.cuda.current_stream().synchronize()
+    return out

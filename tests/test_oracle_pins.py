@@ -193,3 +193,14 @@ def test_join_count_map_independent(orc):
         offB, kB, _ = orc.build(b, V, seed)
         sizes.add(orc.join_count(offA, kA, offB, kB, V)[0])
     assert len(sizes) == 1
+
+
+def test_bucket_counts_is_the_histogram_of_the_bucket_map(orc):
+    # the large-table checks compare GPU offsets with this histogram's
+    # exclusive prefix; it must equal the build's offsets and numpy's count
+    keys = dg.dup_keys_u32(50_000, 3, 17)
+    for V in (1, 97, 1 << 12):
+        c = orc.bucket_counts(keys, V, seed=5)
+        assert np.array_equal(c, np.bincount(orc.buckets(keys, V, 5).astype(np.int64), minlength=V))
+        off, _, _ = orc.build(keys, V, 5)
+        assert np.array_equal(np.concatenate([[0], np.cumsum(c)]).astype(np.uint32), off)
