@@ -24,7 +24,10 @@ Other workloads (one JSON line each, same keys), chosen by --workload:
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
 
-Prints ONE JSON line on rank 0.
+Prints ONE JSON line on rank 0.  With the default workload on one GPU the
+line also carries a "workloads" object: a short run (--workload-steps timed
+steps after 3 warm-ups) of each other workload, with its own value, phases,
+roofline and CPU baseline (--no-workloads leaves it out).
 """
 from __future__ import annotations
 
@@ -72,6 +75,9 @@ def parse():
     ap.add_argument("--cpu-mt-log2n", type=int, default=24,
                     help="sample size of the multithreaded CPU HashGraph (log2 keys); 0 = skip it")
     ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed runs of the per-table loop")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="headline only: skip the other workloads the default line reports under 'workloads'")
+    ap.add_argument("--workload-steps", type=int, default=5, help="timed steps of each secondary workload")
     a = ap.parse_args()
     if a.log2n is None:
         a.log2n = 20 if a.workload == "plain" else 28
@@ -781,15 +787,50 @@ def run_learned(c: Ctx):
                   cpu_baseline=cpu, e2e=None, gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
 
 
+RUNNERS = {"scale": run_scale, "plain": run_scale, "join": run_join, "batched": run_batched, "learned": run_learned}
+
+
+def run_secondary(c: Ctx) -> dict:
+    """The other workloads, each a short run of its own (warm-up, timed
+    steps, CPU baseline), reported beside the headline."""
+    import copy
+    out = {}
+    base = c.args
+    for name in ("plain", "join", "batched", "learned"):
+        a = copy.copy(base)
+        a.workload = name
+        a.steps = max(1, base.workload_steps)
+        a.warmup = max(3, min(base.warmup, 3))
+        a.log2n = 20 if name == "plain" else 28
+        a.log2v = None
+        a.dup = 0.0
+        a.e2e_steps = 0
+        a.plain_steps = 1
+        c.args = a
+        try:
+            t0 = time.perf_counter()
+            d = RUNNERS[name](c)
+            d["wall_s"] = round(time.perf_counter() - t0, 1)
+            for k in ("gpu", "n_gpus", "vs_baseline", "data", "higher_is_better"):
+                d.pop(k, None)
+            out[name] = d
+        except Exception as e:   # a secondary workload must not take the headline down
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        finally:
+            c.args = base
+            c.torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
     c = Ctx(args)
-    fn = {"scale": run_scale, "plain": run_scale, "join": run_join, "batched": run_batched,
-          "learned": run_learned}[args.workload]
-    line = fn(c)
+    line = RUNNERS[args.workload](c)
+    if args.workload == "scale" and not args.no_workloads and c.world == 1:
+        line["workloads"] = run_secondary(c)
     if c.rank == 0:
         print(json.dumps(line), flush=True)
     if c.world > 1:

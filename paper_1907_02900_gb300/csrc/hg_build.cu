@@ -145,11 +145,17 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const K* __restrict__ key
   constexpr int per = 16 / sizeof(K);
   const uint64_t c0 = (uint64_t)blockIdx.x * chunk;
   const uint64_t c1 = min(c0 + chunk, n);
-  const uint64_t v0 = c0 / per, v1 = c1 / per;
-  const uint4* kv = reinterpret_cast<const uint4*>(keys);
+  // 16-byte vector loads between the first and the last 16-byte address
+  // boundary of the chunk (keys may start anywhere: a slab of a larger
+  // build), single loads before and after
+  const uint64_t off = ((uintptr_t)keys / sizeof(K)) % per;
+  const uint64_t y0 = (c0 + off + per - 1) / per * per, y1 = (c1 + off) / per * per;
+  const uint64_t b0 = y1 > y0 ? y0 - off : c1, b1 = y1 > y0 ? y1 - off : c1;
+  const uint4* kv = reinterpret_cast<const uint4*>(keys + b0);
+  const uint64_t nv = (b1 - b0) / per;
   const uint32_t bd = blockDim.x;
-  uint64_t v = v0 + threadIdx.x;
-  for (; v + 3 * (uint64_t)bd < v1; v += 4 * (uint64_t)bd) {
+  uint64_t v = threadIdx.x;
+  for (; v + 3 * (uint64_t)bd < nv; v += 4 * (uint64_t)bd) {
     uint4 x[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) x[u] = __ldcs(kv + v + u * bd);
@@ -157,20 +163,20 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const K* __restrict__ key
     for (int u = 0; u < 4; ++u) {
       K k[per];
       unpack16<K>(x[u], k);
-      const uint32_t p0 = (uint32_t)((v + u * bd) * per);
+      const uint32_t p0 = (uint32_t)(b0 + (v + u * bd) * per);
 #pragma unroll
       for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e], p0 + e) >> s], 1u);
     }
   }
-  for (; v < v1; v += bd) {
+  for (; v < nv; v += bd) {
     K k[per];
     unpack16<K>(__ldcs(kv + v), k);
-    const uint32_t p0 = (uint32_t)(v * per);
+    const uint32_t p0 = (uint32_t)(b0 + v * per);
 #pragma unroll
     for (int e = 0; e < per; ++e) atomicAdd(&hist[map(k[e], p0 + e) >> s], 1u);
   }
-  for (uint64_t i = max(v1 * per, c0) + threadIdx.x; i < c1; i += bd)
-    atomicAdd(&hist[map(keys[i], (uint32_t)i) >> s], 1u);
+  for (uint64_t i = c0 + threadIdx.x; i < b0; i += bd) atomicAdd(&hist[map(keys[i], (uint32_t)i) >> s], 1u);
+  for (uint64_t i = b1 + threadIdx.x; i < c1; i += bd) atomicAdd(&hist[map(keys[i], (uint32_t)i) >> s], 1u);
   __syncthreads();
   uint32_t* row = H + (uint64_t)blockIdx.x * nbins;
   for (uint32_t i = threadIdx.x; i < nbins; i += bd) row[i] = hist[i];
@@ -377,16 +383,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
   };
   auto issue = [&](const Ref& r, int buf) {
     if (threadIdx.x == 0) {
-      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(r.t0, r.t1);
+      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, r.t0, r.t1);
       uint32_t bytes = sk_.bytes();
       TileSpan<4> si_{};
       if (has_ids) {
-        si_ = tile_span<4>(r.t0, r.t1);
+        si_ = tile_span<4>(a.in_i, r.t0, r.t1);
         bytes += si_.bytes();
       }
       mbar_arrive_expect_tx(&bar[buf], bytes);
-      if (sk_.body) tma_load_1d(kin0 + buf * TB, a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
-      if (has_ids && si_.body) tma_load_1d(iin0 + buf * TB, a.in_i + si_.a0, si_.bytes(), &bar[buf]);
+      if (sk_.body) tma_load_1d(kin0 + buf * TB + sk_.dst(), a.in_k + sk_.b0, sk_.bytes(), &bar[buf]);
+      if (has_ids && si_.body) tma_load_1d(iin0 + buf * TB + si_.dst(), a.in_i + si_.b0, si_.bytes(), &bar[buf]);
     }
   };
 
@@ -408,14 +414,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
     const Ref nxt = next_of(cur);
     if (nxt.ok) issue(nxt, buf ^ 1);
     if (!mbar_wait_block(&bar[buf], (it >> 1) & 1u, a.status)) return;
-    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(cur.t0, cur.t1);
+    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, cur.t0, cur.t1);
     TileSpan<4> si_{};
-    if (has_ids) si_ = tile_span<4>(cur.t0, cur.t1);
-    // elements past the last 16-byte boundary (only where a tile ends
-    // unaligned) come in by plain loads; the barrier is needed only then
-    bool sync_needed = (sk_.a0 + sk_.body < cur.t1) || (has_ids && si_.a0 + si_.body < cur.t1);
-    load_tail<sizeof(K)>(kin0 + buf * TB, a.in_k, sk_);
-    if (has_ids) load_tail<4>(iin0 + buf * TB, a.in_i, si_);
+    if (has_ids) si_ = tile_span<4>(a.in_i, cur.t0, cur.t1);
+    // elements outside the 16-byte boundaries (only where a tile starts or
+    // ends unaligned) come in by plain loads; the barrier is needed only then
+    bool sync_needed = sk_.edges() || (has_ids && si_.edges());
+    load_edges<sizeof(K)>(kin0 + buf * TB, a.in_k, sk_);
+    if (has_ids) load_edges<4>(iin0 + buf * TB, a.in_i, si_);
     if (cur.j != cur_j) {  // cursors are first read after tile_partition_fast's first barrier
       cur_j = cur.j;
       const uint32_t item = blockIdx.x + cur.j * gridDim.x;
@@ -434,8 +440,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
     }
     if (sync_needed) __syncthreads();  // block-uniform condition
     const uint32_t cnt = (uint32_t)(cur.t1 - cur.t0);
-    const K* kk = kin0 + buf * TB + (cur.t0 - sk_.a0);
-    const uint32_t* ii = has_ids ? iin0 + buf * TB + (cur.t0 - si_.a0) : nullptr;
+    const K* kk = kin0 + buf * TB + sk_.lead;
+    const uint32_t* ii = has_ids ? iin0 + buf * TB + si_.lead : nullptr;
     K key[IPT];
     uint32_t val[IPT], dig[IPT];
 #pragma unroll
@@ -600,11 +606,11 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   auto issue = [&](uint32_t j, int buf) {
     if (threadIdx.x == 0) {
       const uint64_t k0 = bl_start[j], k1 = k0 + bl_size[j];
-      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(k0, k1);
-      const TileSpan<4> si_ = tile_span<4>(k0, k1);
+      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, k0, k1);
+      const TileSpan<4> si_ = tile_span<4>(a.in_i, k0, k1);
       mbar_arrive_expect_tx(&bar[buf], sk_.bytes() + si_.bytes());
-      if (sk_.body) tma_load_1d(kin0 + (size_t)buf * EB, a.in_k + sk_.a0, sk_.bytes(), &bar[buf]);
-      if (si_.body) tma_load_1d(iin0 + (size_t)buf * EB, a.in_i + si_.a0, si_.bytes(), &bar[buf]);
+      if (sk_.body) tma_load_1d(kin0 + (size_t)buf * EB + sk_.dst(), a.in_k + sk_.b0, sk_.bytes(), &bar[buf]);
+      if (si_.body) tma_load_1d(iin0 + (size_t)buf * EB + si_.dst(), a.in_i + si_.b0, si_.bytes(), &bar[buf]);
     }
   };
   if (threadIdx.x == 0) {
@@ -630,16 +636,16 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
     if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
     const uint32_t E = bl_size[jb], start = bl_start[jb];
-    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(start, (uint64_t)start + E);
-    const TileSpan<4> si_ = tile_span<4>(start, (uint64_t)start + E);
+    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, start, (uint64_t)start + E);
+    const TileSpan<4> si_ = tile_span<4>(a.in_i, start, (uint64_t)start + E);
     K* const kb_ = kin0 + (size_t)buf * EB;
     uint32_t* const ib_ = iin0 + (size_t)buf * EB;
-    load_tail<sizeof(K)>(kb_, a.in_k, sk_);
-    load_tail<4>(ib_, a.in_i, si_);
-    if (sk_.a0 + sk_.body < (uint64_t)start + E || si_.a0 + si_.body < (uint64_t)start + E)
-      __syncthreads();  // tail elements came in by plain loads (block-uniform condition)
-    const K* kk = kb_ + (start - sk_.a0);
-    const uint32_t* ii = ib_ + (start - si_.a0);
+    load_edges<sizeof(K)>(kb_, a.in_k, sk_);
+    load_edges<4>(ib_, a.in_i, si_);
+    if (sk_.edges() || si_.edges())
+      __syncthreads();  // edge elements came in by plain loads (block-uniform condition)
+    const K* kk = kb_ + sk_.lead;
+    const uint32_t* ii = ib_ + si_.lead;
     // 1. local buckets and counts
     for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
       const uint32_t l = map(kk[e], ii[e]) - (uint32_t)bucket0;

@@ -172,13 +172,31 @@ def zipf_cdf(n_distinct: int, s: float = 1.0) -> np.ndarray:
     return c / c[-1]
 
 
+def _zipf1_inverse(cdf: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """searchsorted(cdf, u, 'right') for the Zipf(1) CDF, found from a
+    closed-form first guess: H_m is close to ln(m + 1/2) + 0.5772, so the
+    smallest m with H_m > u * H_n is about exp(u * H_n - 0.5772) - 1/2 and the
+    index (m - 1) about floor(exp(u * H_n - 0.5772) - 0.5).  A guess k is kept
+    where it is the exact index (cdf[k-1] <= u < cdf[k]); the few others (a
+    fraction of a percent) take the binary search."""
+    nd = len(cdf)
+    h_n = np.log(nd + 0.5) + 0.5772156649015329
+    k = np.clip(np.floor(np.exp(u * h_n - 0.5772156649015329) - 0.5), 0, nd - 1).astype(np.int64)
+    bad = cdf[k] <= u
+    bad |= (k > 0) & (cdf[np.maximum(k - 1, 0)] > u)
+    if bad.any():
+        k[bad] = np.searchsorted(cdf, u[bad], side="right")
+    return k
+
+
 def zipf_ranks(n: int, n_distinct: int, seed: int, s: float = 1.0, start: int = 0,
                cdf: np.ndarray | None = None) -> np.ndarray:
-    """Ranks in [1, n_distinct] drawn by inverse CDF (binary search)."""
+    """Ranks in [1, n_distinct] drawn by inverse CDF: the rank of u is
+    searchsorted(cdf, u, side='right') + 1 (s = 1 uses an exact shortcut)."""
     if cdf is None:
         cdf = zipf_cdf(n_distinct, s)
     u = unit_double(splitmix64_range(seed, STREAM_ZIPF, start, n))
-    r = np.searchsorted(cdf, u, side="right")
+    r = _zipf1_inverse(cdf, u) if s == 1.0 else np.searchsorted(cdf, u, side="right")
     return np.minimum(r, n_distinct - 1).astype(np.uint64) + U64(1)
 
 

@@ -85,3 +85,12 @@ def test_batched_sizes_total_and_shape():
     # log-uniform: log2 sizes spread evenly over [10, 22)
     h, _ = np.histogram(np.log2(raw), bins=12, range=(10, 22))
     assert h.min() > 700 and h.max() < 980
+
+
+def test_zipf_inverse_shortcut_equals_binary_search():
+    # the s = 1 shortcut must draw exactly the ranks of the binary search
+    for nd in (1, 2, 3, 100, 4000, 1 << 17):
+        cdf = dg.zipf_cdf(nd)
+        u = dg.unit_double(dg.splitmix64_range(5, dg.STREAM_ZIPF, 0, 1 << 18))
+        u = np.concatenate([u, [0.0, np.nextafter(1.0, 0), cdf[0], np.nextafter(cdf[0], 0), 1.0]])
+        assert np.array_equal(dg._zipf1_inverse(cdf, u), np.searchsorted(cdf, u, side="right")), nd
