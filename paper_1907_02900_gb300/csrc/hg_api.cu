@@ -163,6 +163,8 @@ hg_status hg_probe(const hg_config* cfg, const hg_table* table, const void* d_qu
 
 size_t hg_probe_workspace_size(const hg_config* cfg, uint64_t table_n, uint64_t q) {
   if (validate_config(cfg) != HG_OK) return 0;
+  SlabProbePlan sp{};
+  if (make_slab_probe_plan(cfg, table_n, q, &sp)) return sp.total;
   ProbePlan p{};
   if (!make_probe_plan(cfg, table_n, q, &p)) return 0;
   return p.total;
@@ -179,14 +181,18 @@ hg_status hg_probe_binned(const hg_config* cfg, const hg_table* table, const voi
   const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
   if (!aligned(d_queries, 16) || !aligned(table->d_keys, kb) || !aligned(d_counts, 4) || !aligned(d_ws, 256))
     return HG_ERR_INVALID_ARG;
+  SlabProbePlan sp{};
+  const bool slabs = make_slab_probe_plan(cfg, table->n, q, &sp);
   ProbePlan p{};
-  if (!make_probe_plan(cfg, table->n, q, &p)) return HG_ERR_UNSUPPORTED;
-  if (ws_bytes < p.total) return HG_ERR_WORKSPACE_TOO_SMALL;
+  if (!slabs && !make_probe_plan(cfg, table->n, q, &p)) return HG_ERR_UNSUPPORTED;
+  if (ws_bytes < (slabs ? sp.total : p.total)) return HG_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
   if (q == 0) return HG_OK;
   return dispatch_key_map(cfg, [&](auto k, auto map) -> hg_status {
     using K = decltype(k);
+    if (slabs)
+      return probe_slabs<K>(cfg, sp, table, (const K*)d_queries, q, d_counts, (uint8_t*)d_ws, st, map);
     return probe_binned_impl<K>(p, cfg->num_buckets, table, (const K*)d_queries, q, d_counts, (uint8_t*)d_ws, st,
                                 map);
   });

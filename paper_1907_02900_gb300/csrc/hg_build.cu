@@ -440,8 +440,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
     }
     if (sync_needed) __syncthreads();  // block-uniform condition
     const uint32_t cnt = (uint32_t)(cur.t1 - cur.t0);
-    const K* kk = kin0 + buf * TB + sk_.lead;
-    const uint32_t* ii = has_ids ? iin0 + buf * TB + si_.lead : nullptr;
+    const K* kk = kin0 + buf * TB + sk_.lead();
+    const uint32_t* ii = has_ids ? iin0 + buf * TB + si_.lead() : nullptr;
     K key[IPT];
     uint32_t val[IPT], dig[IPT];
 #pragma unroll
@@ -492,6 +492,7 @@ struct BinArgs {
   const uint32_t* BS;
   uint64_t V;
   uint32_t nbins, s, emax;
+  uint32_t emin;      // bins of at most emin edges are another launch's (0: none)
   uint32_t pos_base;  // added to every offset written (position of element 0 in the CSR arrays)
   int nbuf;  // staging buffers: 2 = next bin prefetched during this one
   uint32_t* status;
@@ -536,6 +537,34 @@ __device__ __forceinline__ void warp_rank_positions(uint16_t* opos, uint32_t beg
   __syncwarp();
 }
 
+// The same ranking by id instead of bin position, for bins whose tiles were
+// partitioned in any order (the ids are then input positions, distinct):
+// every lane holds up to KR (slot, id) pairs, counts the bucket's ids below
+// each of them (all lanes read the same slot and id, broadcasts) and stores
+// each slot at its rank.
+template <int KR>
+__device__ __forceinline__ void warp_rank_ids(uint16_t* opos, const uint32_t* ii, uint32_t beg, uint32_t end,
+                                              uint32_t lane) {
+  uint32_t p[KR], id[KR], r[KR];
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const uint32_t i = beg + lane + 32u * k;
+    p[k] = i < end ? (uint32_t)opos[i] : 0u;
+    id[k] = i < end ? ii[p[k]] : 0xffffffffu;
+    r[k] = 0;
+  }
+  for (uint32_t i = beg; i < end; ++i) {
+    const uint32_t x = ii[opos[i]];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) r[k] += x < id[k];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < KR; ++k)
+    if (beg + lane + 32u * k < end) opos[beg + r[k]] = (uint16_t)p[k];
+  __syncwarp();
+}
+
 // Shared memory of k_binbuild: staging buffers of keys and ids, the local
 // bucket array (LB), slot order (u16), packed u16 bucket counters, the list
 // of long buckets, kBinBitmapWarps position bitmaps and small control state.
@@ -561,8 +590,12 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 // LB: the local buckets of step 1 are kept for step 3 (else recomputed).
 // ANY: the partitions ranked tiles in any order (see k_partition), so the
 // bin positions no longer follow the input order; every bucket of two or
-// more edges is then ranked by id (an input position, distinct) instead,
-// whatever its length.
+// more edges is then ranked by id (an input position, distinct) instead:
+// in registers by one warp for 33 .. kBinRankBucket edges (step 4), edge by
+// edge otherwise (step 5).
+// A bin takes this kernel when emin < E <= emax: one launch covers the bins
+// that fit its double-buffered staging, a second, single-buffered launch
+// (twice the staging room) the larger ones up to its own emax.
 template <typename K, typename Map, int NWB, int MINB, bool LB, bool ANY>
 __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map map) {
   if (a.order != nullptr && ((*(volatile const uint32_t*)a.order == 0u) != ANY)) return;
@@ -600,7 +633,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   }
   __syncthreads();
   auto skip = [&](uint32_t j) {
-    while (j < nmine && bl_size[j] > a.emax) ++j;
+    while (j < nmine && (bl_size[j] > a.emax || bl_size[j] <= a.emin)) ++j;
     return j;
   };
   auto issue = [&](uint32_t j, int buf) {
@@ -644,8 +677,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     load_edges<4>(ib_, a.in_i, si_);
     if (sk_.edges() || si_.edges())
       __syncthreads();  // edge elements came in by plain loads (block-uniform condition)
-    const K* kk = kb_ + sk_.lead;
-    const uint32_t* ii = ib_ + si_.lead;
+    const K* kk = kb_ + sk_.lead();
+    const uint32_t* ii = ib_ + si_.lead();
     // 1. local buckets and counts
     for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
       const uint32_t l = map(kk[e], ii[e]) - (uint32_t)bucket0;
@@ -666,8 +699,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       uint32_t base = block_excl_scan_nt<uint32_t>(sum, wsum);
       for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
-        if (!ANY && lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
-        if (!ANY && hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
+        if (lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
+        if (hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
         cnt[w] = base | ((base + lo) << 16);
         base += lo + hi;
       }
@@ -692,12 +725,18 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
         const uint32_t v = heavy[h];
         const uint32_t end = (cnt[v >> 1] >> ((v & 1u) << 4)) & 0xffffu;
         const uint32_t beg = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
-        if (end - beg <= 64) warp_rank_positions<2>(opos, beg, end, lane);
-        else if (end - beg <= 128) warp_rank_positions<4>(opos, beg, end, lane);
-        else if (end - beg <= kBinRankBucket) warp_rank_positions<kBinRankBucket / 32>(opos, beg, end, lane);
+        if (ANY) {  // by id; longer buckets are ranked edge by edge in step 5
+          if (end - beg <= 64) warp_rank_ids<2>(opos, ii, beg, end, lane);
+          else if (end - beg <= 128) warp_rank_ids<4>(opos, ii, beg, end, lane);
+          else if (end - beg <= kBinRankBucket) warp_rank_ids<kBinRankBucket / 32>(opos, ii, beg, end, lane);
+        } else {
+          if (end - beg <= 64) warp_rank_positions<2>(opos, beg, end, lane);
+          else if (end - beg <= 128) warp_rank_positions<4>(opos, beg, end, lane);
+          else if (end - beg <= kBinRankBucket) warp_rank_positions<kBinRankBucket / 32>(opos, beg, end, lane);
+        }
       }
     }
-    if (nh > 0 && warp < NBM) {
+    if (!ANY && nh > 0 && warp < NBM) {
       // each of the first NBM warps owns one bitmap of E bits
       const uint32_t nbits_words = (E + 31) >> 5;
       uint32_t* bm = bitmaps + warp * bm_words;
@@ -746,7 +785,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
       uint32_t dst = j;
       if (ANY) {
-        if (end - beg > 1) {
+        if (end - beg > 1 && (end - beg <= kBinSmallBucket || end - beg > kBinRankBucket)) {
           dst = beg;
           for (uint32_t i = beg; i < end; ++i) dst += ii[opos[i]] < id;
         }
@@ -776,6 +815,8 @@ struct BinCfg {
   int nbuf;
   bool lb;
   size_t smem;
+  uint32_t emax_wide;  // largest bin of the single-buffered second launch (<= emax: none)
+  size_t smem_wide;
 };
 // Two 512-thread CTAs per SM (local buckets recomputed, no prefetch) measured
 // slower than one 1024-thread CTA that keeps them and prefetches the next bin
@@ -814,6 +855,17 @@ static BinCfg bin_config(const Plan& p, bool recompute) {
   if (c.smem > (size_t)di.max_smem_optin) {
     c.nbuf = 1;
     c.smem = bin_smem_bytes(p.kb, p.emax, p.s, 1, true);
+  }
+  // the largest bin one single-buffered CTA can hold (slot indexes are 16-bit)
+  c.emax_wide = 0;
+  c.smem_wide = 0;
+  if (c.nbuf == 2 && di.max_smem_optin > 0) {
+    uint32_t e = 65504;
+    while (e > p.emax && bin_smem_bytes(p.kb, e, p.s, 1, true) > (size_t)di.max_smem_optin) e -= 32;
+    if (e > p.emax) {
+      c.emax_wide = e;
+      c.smem_wide = bin_smem_bytes(p.kb, e, p.s, 1, true);
+    }
   }
   return c;
 }
@@ -1197,7 +1249,10 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     h.rowdesc = (uint32_t*)(ws + p.o_rowdesc);
     h.max_rows = p.max_rows;
     h.status = status;
-    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, bc.emax, ovf, &hdr->ovf_count, offsets, p.V,
+    // bins above the largest the shared-memory bin build takes (the second,
+    // single-buffered launch included) go to the oversized-bin kernels
+    k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, std::max(bc.emax, bc.emax_wide), ovf, &hdr->ovf_count,
+                                    offsets, p.V,
                                     pos_base + (uint32_t)p.n, h, any_order ? &hdr->order_mode : nullptr);
   }
 
@@ -1289,10 +1344,18 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     grid = std::max<unsigned>(grid, (p.nbins + kMaxBinsPerCta - 1) / kMaxBinsPerCta);
     HG_TRACE("k_binbuild", st);
     auto launch = [&](auto kern, auto kany, unsigned threads) {
-      set_smem_once(kern, bc.smem);
-      set_smem_once(kany, bc.smem);
+      set_smem_once(kern, std::max(bc.smem, bc.smem_wide));
+      set_smem_once(kany, std::max(bc.smem, bc.smem_wide));
       if (any_order) kany<<<grid, threads, bc.smem, st>>>(ba, map);
       kern<<<grid, threads, bc.smem, st>>>(ba, map);
+      if (bc.emax_wide > bc.emax) {  // bins above emax, single-buffered
+        BinArgs<K> bw = ba;
+        bw.emin = bc.emax;
+        bw.emax = bc.emax_wide;
+        bw.nbuf = 1;
+        if (any_order) kany<<<grid, threads, bc.smem_wide, st>>>(bw, map);
+        kern<<<grid, threads, bc.smem_wide, st>>>(bw, map);
+      }
     };
     if (bc.per_sm == 2) {
       if (bc.lb)
@@ -1781,6 +1844,124 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   return last_launch_status();
 }
 
+bool make_slab_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, SlabProbePlan* p) {
+  const uint64_t V = cfg->num_buckets;
+  if (V <= (1ull << kSlabProbeLog2) || q == 0) return false;
+  const DevInfo& di = dev_info();
+  const int kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  p->V = V;
+  p->q = q;
+  p->Ls = kSlabProbeLog2;
+  p->S = (uint32_t)((V + (1ull << p->Ls) - 1) >> p->Ls);
+  const int sms = std::max(di.sms, 1);
+  // chunks are whole blocks of queries, as in the binned probe (its merge
+  // relies on it)
+  uint64_t chunk = std::max<uint64_t>(kPartTile, (q + 2 * sms - 1) / (2 * sms));
+  chunk = (chunk + kQueryBlock - 1) / kQueryBlock * kQueryBlock;
+  p->chunk = chunk;
+  p->G = (uint32_t)std::max<uint64_t>(1, (q + chunk - 1) / chunk);
+  hg_config cs = *cfg;
+  cs.num_buckets = 1ull << p->Ls;
+  if (!make_probe_plan(&cs, table_n, q, &p->sub)) return false;
+  size_t o = sizeof(WsHeader);
+  p->o_H = o;   o = align_up(o + (size_t)p->G * p->S * 4);
+  p->o_C = o;   o = align_up(o + (size_t)p->G * p->S * 4);
+  p->o_CT = o;  o = align_up(o + (size_t)p->S * 4);
+  p->o_GS = o;  o = align_up(o + ((size_t)p->S + 1) * 4);
+  p->o_ovf = o; o = align_up(o + (size_t)p->S * 4 + 16);
+  p->o_qk = o;  o = align_up(o + ((size_t)q + 16) * kb);
+  p->o_qi = o;  o = align_up(o + ((size_t)q + 16) * 4);
+  p->o_qc = o;  o = align_up(o + ((size_t)q + 16) * 4);
+  p->o_sub = o; o = align_up(o + p->sub.total);
+  p->total = o;
+  return true;
+}
+
+template <typename K, typename Map>
+hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_table* t, const K* queries,
+                      uint64_t q, uint32_t* counts, uint8_t* ws, cudaStream_t st, Map map) {
+  WsHeader* hdr = (WsHeader*)ws;
+  uint32_t* H = (uint32_t*)(ws + p.o_H);
+  uint32_t* C = (uint32_t*)(ws + p.o_C);
+  uint32_t* CT = (uint32_t*)(ws + p.o_CT);
+  uint32_t* GS = (uint32_t*)(ws + p.o_GS);
+  uint32_t* ovf = (uint32_t*)(ws + p.o_ovf);
+  K* qk = (K*)(ws + p.o_qk);
+  uint32_t* qi = (uint32_t*)(ws + p.o_qi);
+  uint32_t* qc = (uint32_t*)(ws + p.o_qc);
+  uint8_t* sub = ws + p.o_sub;
+  const DevInfo& di = dev_info();
+  // 1. queries grouped by slab (bucket >> Ls), in whole query blocks
+  {
+    const size_t sm = hist_stage_offset(p.S) + Map::kStageBytes;
+    auto kern = k_hist<K, Map>;
+    set_smem_once(kern, sm);
+    HG_TRACE("k_hist_Q", st);
+    kern<<<p.G, kHistThreads, sm, st>>>(queries, q, p.chunk, p.Ls, p.S, 0, p.S, H, C, map,
+                                        (uint32_t)Map::kStageBytes);
+    k_colscan<<<1, 256, 0, st>>>(C, p.G, p.S, CT);
+    k_scan_bins<<<1, 1024, 0, st>>>(CT, p.S, GS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.S, 0, (uint32_t)q,
+                                    HugeArgs{}, nullptr);
+  }
+  {
+    PartArgs<K> pa{};
+    pa.in_k = queries;
+    pa.in_i = nullptr;  // ids = query positions
+    pa.out_k = qk;
+    pa.out_i = qi;
+    pa.n = q;
+    pa.chunk = p.chunk;
+    pa.G = p.G;
+    pa.s = p.Ls;
+    pa.sshift = 0;
+    pa.nbins = p.S;
+    pa.nsb = p.S;
+    pa.H = H;
+    pa.C = C;
+    pa.CT = CT;
+    pa.BS = GS;
+    pa.status = &hdr->status;
+    const size_t own = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW);
+    pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
+    auto kern = k_partition<K, Map, false, part_ipt_queries<K>(), kPartNW, kPartMinBlocksQ, true>;
+    set_smem_once(kern, own + pa.stage_bytes);
+    HG_TRACE("k_partition_Q", st);
+    kern<<<p.G, kPartNW * 32, own + pa.stage_bytes, st>>>(pa, map);
+  }
+  // 2. slab query counts to the host, then the binned probe of every slab
+  uint32_t hGS[257];
+  if (cudaMemcpyAsync(hGS, GS, ((size_t)p.S + 1) * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HG_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HG_ERR_CUDA;
+  for (uint32_t sl = 0; sl < p.S; ++sl) {
+    const uint64_t qs = hGS[sl + 1] - hGS[sl];
+    if (qs == 0) continue;
+    const uint64_t b0 = (uint64_t)sl << p.Ls;
+    hg_config cs = *cfg;
+    cs.num_buckets = std::min<uint64_t>(1ull << p.Ls, p.V - b0);
+    ProbePlan ps{};
+    if (!make_probe_plan(&cs, t->n, qs, &ps) || ps.total > p.sub.total) return HG_ERR_UNSUPPORTED;
+    hg_table ts = *t;
+    ts.d_offsets = t->d_offsets + b0;  // offsets are positions in the whole table's key array
+    Map ms = map;
+    ms.slab_base = (uint32_t)b0;
+    if (cudaMemsetAsync(sub, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
+    hg_status rc = probe_binned_impl<K, Map>(ps, cs.num_buckets, &ts, qk + hGS[sl], qs, qc + hGS[sl], sub, st, ms);
+    if (rc != HG_OK) return rc;
+    k_carry_status<<<1, 1, 0, st>>>(&((WsHeader*)sub)->status, &hdr->status);
+  }
+  // 3. counts back to query order
+  {
+    const uint64_t blocks = (q + kQueryBlock - 1) / kQueryBlock;
+    const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)2 * di.sms));
+    const uint64_t span = (blocks + grid - 1) / grid * kQueryBlock;
+    auto kern = k_unpermute<1, 8>;
+    set_smem_once(kern, (size_t)kUnpermuteTile * 4);
+    HG_TRACE("k_unpermute", st);
+    kern<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.S, q, span, counts);
+  }
+  return last_launch_status();
+}
+
 // ===========================================================================
 // LSD radix sort of uint64 keys (used for the learned map's key sample):
 // eight stable passes of the same histogram -> scan -> stable tile partition
@@ -1894,6 +2075,8 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
                                        uint32_t*, K*, uint32_t*, uint8_t*, cudaStream_t, M);            \
   template hg_status build_v1<K, M>(uint64_t, uint64_t, const K*, const uint32_t*, uint32_t*, K*,       \
                                     uint32_t*, uint8_t*, cudaStream_t, M);                              \
+  template hg_status probe_slabs<K, M>(const hg_config*, const SlabProbePlan&, const hg_table*, const K*,  \
+                                       uint64_t, uint32_t*, uint8_t*, cudaStream_t, M);                   \
   template hg_status probe_binned_impl<K, M>(const ProbePlan&, uint64_t, const hg_table*, const K*,     \
                                              uint64_t, uint32_t*, uint8_t*, cudaStream_t, M);
 HG_INST(uint32_t, MurmurMap)

@@ -141,6 +141,25 @@ struct ProbePlan {
   size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, total;
 };
 bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePlan* p);
+// Binned probe of a table of more than 2^kSlabProbeLog2 buckets: 128 query
+// groups would leave each group a table slice too large for L2, so the
+// queries are first grouped by slab of 2^kSlabProbeLog2 buckets (the slabs a
+// large build relabels by), each slab's queries take the binned probe
+// against the slab's part of the table, and the counts are merged back to
+// query order.  The slab query counts are read back to the host between the
+// two steps (one stream synchronisation).
+constexpr uint32_t kSlabProbeLog2 = 28;
+struct SlabProbePlan {
+  uint64_t V, q;
+  uint32_t Ls, S, G;
+  uint64_t chunk;
+  ProbePlan sub;  // plan of a slab holding all q queries: the bound of every slab probe's workspace
+  size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, o_sub, total;
+};
+bool make_slab_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, SlabProbePlan* p);
+template <typename K, typename Map>
+hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_table* t, const K* queries,
+                      uint64_t q, uint32_t* counts, uint8_t* ws, cudaStream_t st, Map map);
 size_t radix_sort_workspace_bytes(uint64_t n);
 hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t st);
 template <typename K, typename Map>

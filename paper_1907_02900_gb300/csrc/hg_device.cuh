@@ -514,50 +514,53 @@ __device__ __forceinline__ bool mbar_wait_block(uint64_t* bar, uint32_t parity, 
 }
 
 // Copy elements [k0, k1) of a device array g (element size ES bytes; the
-// base need only be ES-aligned) into smem so that smem[x - k0 + lead] holds
-// element x.  The elements between the first and the last 16-byte address
-// boundary of the range go through one TMA bulk copy (issued by thread 0
-// together with the barrier's expected byte count), into smem at offset
-// b0 - k0 + lead, which lead (0 .. 16/ES - 1) puts on a 16-byte boundary;
-// the fewer than 16 bytes before and after it are loaded by the caller with
-// load_edges() after the wait.  Staging buffers therefore hold 16/ES spare
-// elements.  The address arithmetic makes no assumption on g's alignment
-// (arrays that start inside another array, such as one slab of a larger
-// build, are common).
+// base need only be ES-aligned) into smem so that smem[x - a0] holds element
+// x, where a0 is the last element at or below k0 whose address is 16-byte
+// aligned (a0 may lie below the array start, at -1 .. -(16/ES - 1), when g
+// itself is not 16-byte aligned: the index arithmetic is signed).  One TMA
+// bulk copy (issued by thread 0 together with the barrier's expected byte
+// count) brings the elements from b0 = max(a0, first aligned element inside
+// the array) up to the last 16-byte boundary; elements of [k0, k1) outside
+// it (fewer than 16 bytes at either end, and only at the start of an
+// unaligned array at the front) are loaded by the caller with load_edges()
+// after the wait.  Elements between a0 and k0 that the copy brings along are
+// inside the array and unused.  Staging buffers hold 16/ES spare elements.
+// (Arrays that start inside another array, such as one slab of a larger
+// build, need the unaligned case.)
 template <int ES>
 struct TileSpan {
+  int64_t a0;        // element a0 sits at smem[0]
   uint64_t k0, end;  // the range [k0, end)
   uint64_t b0;       // first element of the bulk copy
   uint64_t body;     // elements copied by TMA: [b0, b0 + body)
-  uint32_t lead;     // element x sits at smem[x - k0 + lead]
   __device__ __forceinline__ uint32_t bytes() const { return (uint32_t)(body * ES); }
-  __device__ __forceinline__ uint32_t dst() const { return (uint32_t)(b0 - k0) + lead; }  // smem index of b0
+  __device__ __forceinline__ uint32_t dst() const { return (uint32_t)((int64_t)b0 - a0); }  // smem index of b0
+  __device__ __forceinline__ uint32_t lead() const { return (uint32_t)((int64_t)k0 - a0); }  // smem index of k0
   __device__ __forceinline__ bool edges() const { return b0 > k0 || b0 + body < end; }
 };
 template <int ES, typename T>
 __device__ __forceinline__ TileSpan<ES> tile_span(const T* g, uint64_t k0, uint64_t k1) {
-  constexpr uint64_t per = 16 / ES;
-  const uint64_t off = ((uintptr_t)g / ES) % per;  // element x has a 16-byte aligned address iff (x + off) % per == 0
+  constexpr int64_t per = 16 / ES;
+  const int64_t off = (int64_t)(((uintptr_t)g / ES) % per);  // (x + off) % per == 0: x has an aligned address
   TileSpan<ES> s;
   s.k0 = k0;
   s.end = k1;
-  const uint64_t y0 = (k0 + off + per - 1) / per * per;
-  const uint64_t y1 = (k1 + off) / per * per;
-  if (y1 > y0) {
-    s.b0 = y0 - off;
-    s.body = y1 - y0;
-    s.lead = (uint32_t)((per - (s.b0 - k0)) % per);
+  s.a0 = ((int64_t)k0 + off) / per * per - off;
+  const int64_t b0 = s.a0 >= 0 ? s.a0 : s.a0 + per;
+  const int64_t b1 = ((int64_t)k1 + off) / per * per - off;
+  if (b1 > b0) {
+    s.b0 = (uint64_t)b0;
+    s.body = (uint64_t)(b1 - b0);
   } else {
     s.b0 = k0;
     s.body = 0;
-    s.lead = 0;
   }
   return s;
 }
 template <int ES, typename T>
 __device__ __forceinline__ void load_edges(T* smem, const T* g, const TileSpan<ES>& s) {
-  for (uint64_t x = s.k0 + threadIdx.x; x < s.b0; x += blockDim.x) smem[x - s.k0 + s.lead] = g[x];
-  for (uint64_t x = s.b0 + s.body + threadIdx.x; x < s.end; x += blockDim.x) smem[x - s.k0 + s.lead] = g[x];
+  for (uint64_t x = s.k0 + threadIdx.x; x < s.b0; x += blockDim.x) smem[(int64_t)x - s.a0] = g[x];
+  for (uint64_t x = s.b0 + s.body + threadIdx.x; x < s.end; x += blockDim.x) smem[(int64_t)x - s.a0] = g[x];
 }
 
 }  // namespace hg

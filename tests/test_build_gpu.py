@@ -291,3 +291,14 @@ def test_any_order_tiles_equal_stable_build(hg, orc, kt):
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
     roff, rk, ri = orc.build(keys, V)
     assert np.array_equal(a[0], roff) and np.array_equal(a[1], rk) and np.array_equal(a[2], ri)
+
+
+@pytest.mark.parametrize("mult", [8, 32])
+def test_build_duplicates_bins_above_the_double_buffered_size(hg, orc, mult):
+    """Keys drawn from [1 .. N/D] at load factor 1: bins of 8192 buckets hold
+    8192 edges on average, with a spread that grows with D, so some exceed
+    the double-buffered bin build (9216 edges) and take the single-buffered
+    second launch; the partitions still rank tiles in any order and every
+    bucket (about D edges) is ranked by id.  Canonical table, byte for byte."""
+    n = (1 << 22) + 7
+    _check_build(hg, orc, dg.dup_keys_u32(n, mult, 15 + mult), 1 << 22)
