@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
 
   map.init();
   map.stage(stage, a.stage_bytes);
+  const uint32_t koff = align_off<sizeof(K)>(a.in_k), ioff = has_ids ? align_off<4>(a.in_i) : 0u;
   for (int i = threadIdx.x; i < rank_words<NW>(); i += blockDim.x) wc[i] = 0;
   const uint64_t nitems = PASS_B ? (uint64_t)a.nsb * a.ngroups : (uint64_t)a.G;
   if (PASS_B) {
@@ -383,11 +384,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
   };
   auto issue = [&](const Ref& r, int buf) {
     if (threadIdx.x == 0) {
-      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, r.t0, r.t1);
+      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(koff, r.t0, r.t1);
       uint32_t bytes = sk_.bytes();
       TileSpan<4> si_{};
       if (has_ids) {
-        si_ = tile_span<4>(a.in_i, r.t0, r.t1);
+        si_ = tile_span<4>(ioff, r.t0, r.t1);
         bytes += si_.bytes();
       }
       mbar_arrive_expect_tx(&bar[buf], bytes);
@@ -414,9 +415,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
     const Ref nxt = next_of(cur);
     if (nxt.ok) issue(nxt, buf ^ 1);
     if (!mbar_wait_block(&bar[buf], (it >> 1) & 1u, a.status)) return;
-    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, cur.t0, cur.t1);
+    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(koff, cur.t0, cur.t1);
     TileSpan<4> si_{};
-    if (has_ids) si_ = tile_span<4>(a.in_i, cur.t0, cur.t1);
+    if (has_ids) si_ = tile_span<4>(ioff, cur.t0, cur.t1);
     // elements outside the 16-byte boundaries (only where a tile starts or
     // ends unaligned) come in by plain loads; the barrier is needed only then
     bool sync_needed = sk_.edges() || (has_ids && si_.edges());
@@ -492,7 +493,8 @@ struct BinArgs {
   const uint32_t* BS;
   uint64_t V;
   uint32_t nbins, s, emax;
-  uint32_t emin;      // bins of at most emin edges are another launch's (0: none)
+  uint32_t emin;      // bins of at most emin edges are another launch's; 0: no lower bound (empty
+                      // bins are built too: their buckets' offsets must be written)
   uint32_t pos_base;  // added to every offset written (position of element 0 in the CSR arrays)
   int nbuf;  // staging buffers: 2 = next bin prefetched during this one
   uint32_t* status;
@@ -565,6 +567,17 @@ __device__ __forceinline__ void warp_rank_ids(uint16_t* opos, const uint32_t* ii
   __syncwarp();
 }
 
+// Compile-time switches (the defaults are the measured choices): the
+// single-buffered second bin-build launch for bins above the double-buffered
+// size, and the register ranking by id of buckets of 33 .. kBinRankBucket
+// edges when the partitions ranked tiles in any order.
+#ifndef HG_BIN_WIDE
+#define HG_BIN_WIDE 1
+#endif
+#ifndef HG_ANY_WARP_RANK
+#define HG_ANY_WARP_RANK 1
+#endif
+
 // Shared memory of k_binbuild: staging buffers of keys and ids, the local
 // bucket array (LB), slot order (u16), packed u16 bucket counters, the list
 // of long buckets, kBinBitmapWarps position bitmaps and small control state.
@@ -593,9 +606,10 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 // more edges is then ranked by id (an input position, distinct) instead:
 // in registers by one warp for 33 .. kBinRankBucket edges (step 4), edge by
 // edge otherwise (step 5).
-// A bin takes this kernel when emin < E <= emax: one launch covers the bins
-// that fit its double-buffered staging, a second, single-buffered launch
-// (twice the staging room) the larger ones up to its own emax.
+// A bin takes this kernel when E <= emax and, for emin > 0, E > emin: one
+// launch (emin = 0) covers every bin that fits its double-buffered staging,
+// empty ones included, a second, single-buffered launch (twice the staging
+// room) the larger ones up to its own emax.
 template <typename K, typename Map, int NWB, int MINB, bool LB, bool ANY>
 __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map map) {
   if (a.order != nullptr && ((*(volatile const uint32_t*)a.order == 0u) != ANY)) return;
@@ -623,6 +637,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   uint64_t* bar = (uint64_t*)sp;
 
   map.init();
+  const uint32_t koff = align_off<sizeof(K)>(a.in_k), ioff = align_off<4>(a.in_i);
   // Bins blockIdx.x, +gridDim.x, ...: starts and sizes gathered once, so the
   // loop below needs no global loads to find its next bin.
   const uint32_t nmine = blockIdx.x < a.nbins ? (a.nbins - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;
@@ -633,14 +648,14 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   }
   __syncthreads();
   auto skip = [&](uint32_t j) {
-    while (j < nmine && (bl_size[j] > a.emax || bl_size[j] <= a.emin)) ++j;
+    while (j < nmine && (bl_size[j] > a.emax || (a.emin != 0 && bl_size[j] <= a.emin))) ++j;
     return j;
   };
   auto issue = [&](uint32_t j, int buf) {
     if (threadIdx.x == 0) {
       const uint64_t k0 = bl_start[j], k1 = k0 + bl_size[j];
-      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, k0, k1);
-      const TileSpan<4> si_ = tile_span<4>(a.in_i, k0, k1);
+      const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(koff, k0, k1);
+      const TileSpan<4> si_ = tile_span<4>(ioff, k0, k1);
       mbar_arrive_expect_tx(&bar[buf], sk_.bytes() + si_.bytes());
       if (sk_.body) tma_load_1d(kin0 + (size_t)buf * EB + sk_.dst(), a.in_k + sk_.b0, sk_.bytes(), &bar[buf]);
       if (si_.body) tma_load_1d(iin0 + (size_t)buf * EB + si_.dst(), a.in_i + si_.b0, si_.bytes(), &bar[buf]);
@@ -669,8 +684,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
     if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
     const uint32_t E = bl_size[jb], start = bl_start[jb];
-    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(a.in_k, start, (uint64_t)start + E);
-    const TileSpan<4> si_ = tile_span<4>(a.in_i, start, (uint64_t)start + E);
+    const TileSpan<sizeof(K)> sk_ = tile_span<sizeof(K)>(koff, start, (uint64_t)start + E);
+    const TileSpan<4> si_ = tile_span<4>(ioff, start, (uint64_t)start + E);
     K* const kb_ = kin0 + (size_t)buf * EB;
     uint32_t* const ib_ = iin0 + (size_t)buf * EB;
     load_edges<sizeof(K)>(kb_, a.in_k, sk_);
@@ -699,8 +714,8 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       uint32_t base = block_excl_scan_nt<uint32_t>(sum, wsum);
       for (uint32_t w = w0; w < w1; ++w) {
         const uint32_t x = cnt[w], lo = x & 0xffffu, hi = x >> 16;
-        if (lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
-        if (hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
+        if ((HG_ANY_WARP_RANK || !ANY) && lo > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w);
+        if ((HG_ANY_WARP_RANK || !ANY) && hi > kBinSmallBucket) heavy[atomicAdd(nheavy, 1u)] = (uint16_t)(2 * w + 1);
         cnt[w] = base | ((base + lo) << 16);
         base += lo + hi;
       }
@@ -785,7 +800,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
       uint32_t dst = j;
       if (ANY) {
-        if (end - beg > 1 && (end - beg <= kBinSmallBucket || end - beg > kBinRankBucket)) {
+        if (end - beg > 1 && (!HG_ANY_WARP_RANK || end - beg <= kBinSmallBucket || end - beg > kBinRankBucket)) {
           dst = beg;
           for (uint32_t i = beg; i < end; ++i) dst += ii[opos[i]] < id;
         }
@@ -859,7 +874,7 @@ static BinCfg bin_config(const Plan& p, bool recompute) {
   // the largest bin one single-buffered CTA can hold (slot indexes are 16-bit)
   c.emax_wide = 0;
   c.smem_wide = 0;
-  if (c.nbuf == 2 && di.max_smem_optin > 0) {
+  if (HG_BIN_WIDE && c.nbuf == 2 && di.max_smem_optin > 0) {
     uint32_t e = 65504;
     while (e > p.emax && bin_smem_bytes(p.kb, e, p.s, 1, true) > (size_t)di.max_smem_optin) e -= 32;
     if (e > p.emax) {

@@ -538,16 +538,22 @@ struct TileSpan {
   __device__ __forceinline__ uint32_t lead() const { return (uint32_t)((int64_t)k0 - a0); }  // smem index of k0
   __device__ __forceinline__ bool edges() const { return b0 > k0 || b0 + body < end; }
 };
+// Alignment offset of an array: element x has a 16-byte aligned address iff
+// (x + off) % (16/ES) == 0 (computed once per kernel).
 template <int ES, typename T>
-__device__ __forceinline__ TileSpan<ES> tile_span(const T* g, uint64_t k0, uint64_t k1) {
+__device__ __forceinline__ uint32_t align_off(const T* g) {
+  return (uint32_t)(((uintptr_t)g / ES) & (16 / ES - 1));
+}
+template <int ES>
+__device__ __forceinline__ TileSpan<ES> tile_span(uint32_t off, uint64_t k0, uint64_t k1) {
+  constexpr uint64_t mask = ~(uint64_t)(16 / ES - 1);
   constexpr int64_t per = 16 / ES;
-  const int64_t off = (int64_t)(((uintptr_t)g / ES) % per);  // (x + off) % per == 0: x has an aligned address
   TileSpan<ES> s;
   s.k0 = k0;
   s.end = k1;
-  s.a0 = ((int64_t)k0 + off) / per * per - off;
+  s.a0 = (int64_t)((k0 + off) & mask) - (int64_t)off;
   const int64_t b0 = s.a0 >= 0 ? s.a0 : s.a0 + per;
-  const int64_t b1 = ((int64_t)k1 + off) / per * per - off;
+  const int64_t b1 = (int64_t)((k1 + off) & mask) - (int64_t)off;
   if (b1 > b0) {
     s.b0 = (uint64_t)b0;
     s.body = (uint64_t)(b1 - b0);
