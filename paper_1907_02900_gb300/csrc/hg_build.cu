@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
 
   map.init();
   map.stage(stage, a.stage_bytes);
-  const uint32_t koff = align_off<sizeof(K)>(a.in_k), ioff = has_ids ? align_off<4>(a.in_i) : 0u;
+  const uint32_t koff = align_first<sizeof(K)>(a.in_k), ioff = has_ids ? align_first<4>(a.in_i) : 0u;
   for (int i = threadIdx.x; i < rank_words<NW>(); i += blockDim.x) wc[i] = 0;
   const uint64_t nitems = PASS_B ? (uint64_t)a.nsb * a.ngroups : (uint64_t)a.G;
   if (PASS_B) {
@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   uint64_t* bar = (uint64_t*)sp;
 
   map.init();
-  const uint32_t koff = align_off<sizeof(K)>(a.in_k), ioff = align_off<4>(a.in_i);
+  const uint32_t koff = align_first<sizeof(K)>(a.in_k), ioff = align_first<4>(a.in_i);
   // Bins blockIdx.x, +gridDim.x, ...: starts and sizes gathered once, so the
   // loop below needs no global loads to find its next bin.
   const uint32_t nmine = blockIdx.x < a.nbins ? (a.nbins - blockIdx.x + gridDim.x - 1) / gridDim.x : 0u;

@@ -516,47 +516,47 @@ __device__ __forceinline__ bool mbar_wait_block(uint64_t* bar, uint32_t parity, 
 // Copy elements [k0, k1) of a device array g (element size ES bytes; the
 // base need only be ES-aligned) into smem so that smem[x - a0] holds element
 // x, where a0 is the last element at or below k0 whose address is 16-byte
-// aligned (a0 may lie below the array start, at -1 .. -(16/ES - 1), when g
-// itself is not 16-byte aligned: the index arithmetic is signed).  One TMA
-// bulk copy (issued by thread 0 together with the barrier's expected byte
-// count) brings the elements from b0 = max(a0, first aligned element inside
-// the array) up to the last 16-byte boundary; elements of [k0, k1) outside
-// it (fewer than 16 bytes at either end, and only at the start of an
-// unaligned array at the front) are loaded by the caller with load_edges()
-// after the wait.  Elements between a0 and k0 that the copy brings along are
-// inside the array and unused.  Staging buffers hold 16/ES spare elements.
-// (Arrays that start inside another array, such as one slab of a larger
-// build, need the unaligned case.)
+// aligned.  When g itself is not 16-byte aligned and k0 lies before its first
+// aligned element q, a0 = q - 16/ES lies below the array start (unsigned
+// arithmetic wraps; indexes x - a0 stay small).  One TMA bulk copy (issued by
+// thread 0 together with the barrier's expected byte count) brings the
+// elements from b0 = max(a0, q) up to the last 16-byte boundary at or below
+// k1; elements of [k0, k1) outside it (fewer than 16 bytes at the end, and at
+// the start only before q) are loaded by the caller with load_edges() after
+// the wait.  Elements between a0 and k0 that the copy brings along are inside
+// the array and unused.  Staging buffers hold 16/ES spare elements.  Indexes
+// are 32-bit (every array here has fewer than 2^32 elements).  (Arrays that
+// start inside another array, such as one slab of a larger build, need the
+// unaligned case.)
 template <int ES>
 struct TileSpan {
-  int64_t a0;        // element a0 sits at smem[0]
-  uint64_t k0, end;  // the range [k0, end)
-  uint64_t b0;       // first element of the bulk copy
-  uint64_t body;     // elements copied by TMA: [b0, b0 + body)
-  __device__ __forceinline__ uint32_t bytes() const { return (uint32_t)(body * ES); }
-  __device__ __forceinline__ uint32_t dst() const { return (uint32_t)((int64_t)b0 - a0); }  // smem index of b0
-  __device__ __forceinline__ uint32_t lead() const { return (uint32_t)((int64_t)k0 - a0); }  // smem index of k0
+  uint32_t a0;    // element a0 sits at smem[0]
+  uint32_t k0, end;
+  uint32_t b0;    // first element of the bulk copy
+  uint32_t body;  // elements copied by TMA: [b0, b0 + body)
+  __device__ __forceinline__ uint32_t bytes() const { return body * ES; }
+  __device__ __forceinline__ uint32_t dst() const { return b0 - a0; }   // smem index of b0
+  __device__ __forceinline__ uint32_t lead() const { return k0 - a0; }  // smem index of k0
   __device__ __forceinline__ bool edges() const { return b0 > k0 || b0 + body < end; }
 };
-// Alignment offset of an array: element x has a 16-byte aligned address iff
-// (x + off) % (16/ES) == 0 (computed once per kernel).
+// Index of the first element of g with a 16-byte aligned address (computed
+// once per kernel).
 template <int ES, typename T>
-__device__ __forceinline__ uint32_t align_off(const T* g) {
-  return (uint32_t)(((uintptr_t)g / ES) & (16 / ES - 1));
+__device__ __forceinline__ uint32_t align_first(const T* g) {
+  return (uint32_t)((16 - ((uintptr_t)g & 15)) & 15) / ES;
 }
 template <int ES>
-__device__ __forceinline__ TileSpan<ES> tile_span(uint32_t off, uint64_t k0, uint64_t k1) {
-  constexpr uint64_t mask = ~(uint64_t)(16 / ES - 1);
-  constexpr int64_t per = 16 / ES;
+__device__ __forceinline__ TileSpan<ES> tile_span(uint32_t q, uint64_t k0_, uint64_t k1_) {
+  constexpr uint32_t pm = 16 / ES - 1;
+  const uint32_t k0 = (uint32_t)k0_, k1 = (uint32_t)k1_;
   TileSpan<ES> s;
   s.k0 = k0;
   s.end = k1;
-  s.a0 = (int64_t)((k0 + off) & mask) - (int64_t)off;
-  const int64_t b0 = s.a0 >= 0 ? s.a0 : s.a0 + per;
-  const int64_t b1 = (int64_t)((k1 + off) & mask) - (int64_t)off;
-  if (b1 > b0) {
-    s.b0 = (uint64_t)b0;
-    s.body = (uint64_t)(b1 - b0);
+  s.a0 = k0 - ((k0 - q) & pm);
+  s.b0 = s.a0 > k0 ? s.a0 + pm + 1 : s.a0;  // a0 wrapped below the array start: the copy starts at q
+  const uint32_t b1 = k1 - ((k1 - q) & pm);
+  if (b1 > s.b0 && b1 <= k1) {
+    s.body = b1 - s.b0;
   } else {
     s.b0 = k0;
     s.body = 0;
@@ -565,8 +565,9 @@ __device__ __forceinline__ TileSpan<ES> tile_span(uint32_t off, uint64_t k0, uin
 }
 template <int ES, typename T>
 __device__ __forceinline__ void load_edges(T* smem, const T* g, const TileSpan<ES>& s) {
-  for (uint64_t x = s.k0 + threadIdx.x; x < s.b0; x += blockDim.x) smem[(int64_t)x - s.a0] = g[x];
-  for (uint64_t x = s.b0 + s.body + threadIdx.x; x < s.end; x += blockDim.x) smem[(int64_t)x - s.a0] = g[x];
+  for (uint64_t x = s.k0 + threadIdx.x; x < s.b0; x += blockDim.x) smem[(uint32_t)x - s.a0] = g[x];
+  for (uint64_t x = (uint64_t)s.b0 + s.body + threadIdx.x; x < s.end; x += blockDim.x)
+    smem[(uint32_t)x - s.a0] = g[x];
 }
 
 }  // namespace hg
