@@ -301,6 +301,9 @@ struct PartArgs {
   uint32_t stage_bytes;  // shared memory after the kernel's own, for the bucket map's tables
   // order mode word (null: always stable); see k_partition
   const uint32_t* order;
+  // optional: per tile (tiles start at multiples of the kernel's tile size),
+  // the tile's count of every digit, nbins 16-bit entries per tile
+  uint16_t* tile_counts;
 };
 
 // ANY: tiles ranked by shared-memory atomics, equal digits in any order
@@ -465,7 +468,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_partition(PartArgs<K> a, Map 
                                               a.out_k, a.out_i, 0u);
       else
         tile_partition_any<K, IPT, NW, true>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
-                                             a.out_k, a.out_i, (uint32_t)cur.t0);
+                                             a.out_k, a.out_i, (uint32_t)cur.t0,
+                                             a.tile_counts ? a.tile_counts + (cur.t0 / TILE) * a.nbins : nullptr);
     } else {
       if (has_ids)
         tile_partition_fast<K, IPT, NW, false>(key, val, dig, cnt, ndig, sk, sv, sd, wc, dstart, cursor, wsum,
@@ -577,13 +581,21 @@ __device__ __forceinline__ void warp_rank_ids(uint16_t* opos, const uint32_t* ii
 #ifndef HG_ANY_WARP_RANK
 #define HG_ANY_WARP_RANK 1
 #endif
+// Slots of buckets of 3 .. 32 edges (and longer ones no warp ranked) are
+// ranked in a second, compact pass over a list of them instead of inside the
+// main write loop, where every warp would wait for its longest bucket.
+#ifndef HG_BIN_PEND
+#define HG_BIN_PEND 0
+#endif
+constexpr uint32_t kBinPendDiv = 2;  // list capacity: emax / kBinPendDiv slots (overflow ranked inline)
 
 // Shared memory of k_binbuild: staging buffers of keys and ids, the local
 // bucket array (LB), slot order (u16), packed u16 bucket counters, the list
 // of long buckets, kBinBitmapWarps position bitmaps and small control state.
 size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
   size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + (lb ? (size_t)emax * 2 : 0) + (size_t)emax * 2 +
-             (((size_t)1 << s) + 1) / 2 * 4 + ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2;
+             (((size_t)1 << s) + 1) / 2 * 4 + ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2 +
+             (HG_BIN_PEND ? ((size_t)emax / kBinPendDiv + 2) * 2 : 0);
   b = align_up(b, 16) + (size_t)kBinBitmapWarps * ((emax + 31) / 32) * 4;
   return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
 }
@@ -625,13 +637,15 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   uint16_t* opos = (uint16_t*)sp; sp += (size_t)a.emax * 2;
   uint32_t* cnt = (uint32_t*)sp; sp += (((size_t)1 << a.s) + 1) / 2 * 4;
   uint16_t* heavy = (uint16_t*)sp; sp += (size_t)(a.emax / (kBinSmallBucket + 1) + 2) * 2;
+  uint16_t* pend = (uint16_t*)sp; sp += HG_BIN_PEND ? (size_t)(a.emax / kBinPendDiv + 2) * 2 : 0;
+  const uint32_t pend_cap = a.emax / kBinPendDiv;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   const uint32_t bm_words = (a.emax + 31) / 32;
   uint32_t* bitmaps = (uint32_t*)sp;  // NBM bitmaps of bm_words words
   sp += (size_t)NBM * bm_words * 4;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
-  uint32_t* nheavy = (uint32_t*)sp; sp += 16;
+  uint32_t* nheavy = (uint32_t*)sp; sp += 16;  // [0] long buckets, [1] pending slots
   uint32_t* bl_start = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;  // this CTA's bins: start, size
   uint32_t* bl_size = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;
   uint64_t* bar = (uint64_t*)sp;
@@ -680,7 +694,10 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
     const uint32_t nwords = (nb + 1) >> 1;
     for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) cnt[w] = 0;
-    if (threadIdx.x == 0) *nheavy = 0;
+    if (threadIdx.x == 0) {
+      nheavy[0] = 0;
+      nheavy[1] = 0;
+    }
     const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
     if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
     const uint32_t E = bl_size[jb], start = bl_start[jb];
@@ -791,6 +808,22 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     //    stay within a few sectors); a long bucket is already in order.  With
     //    ANY every bucket is ranked by id the same way.
     //    Then the bin's offsets (bucket v starts where bucket v - 1 ends).
+    // Whether slot j's bucket [beg, end) still needs ranking here (longer
+    // ones were put in order in step 4), and its rank.
+    auto loose = [&](uint32_t beg, uint32_t end) {
+      const uint32_t n = end - beg;
+      if (n < 2) return false;
+      if (ANY) return !HG_ANY_WARP_RANK || n <= kBinSmallBucket || n > kBinRankBucket;
+      return n <= kBinSmallBucket;
+    };
+    auto rank_of = [&](uint32_t beg, uint32_t end, uint32_t p, uint32_t id) {
+      uint32_t dst = beg;
+      if (ANY)
+        for (uint32_t i = beg; i < end; ++i) dst += ii[opos[i]] < id;
+      else
+        for (uint32_t i = beg; i < end; ++i) dst += opos[i] < p;
+      return dst;
+    };
     for (uint32_t j = threadIdx.x; j < E; j += blockDim.x) {
       const uint32_t p = opos[j];
       const K key = kk[p];
@@ -799,17 +832,39 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       const uint32_t end = (cnt[l >> 1] >> ((l & 1u) << 4)) & 0xffffu;
       const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
       uint32_t dst = j;
-      if (ANY) {
-        if (end - beg > 1 && (!HG_ANY_WARP_RANK || end - beg <= kBinSmallBucket || end - beg > kBinRankBucket)) {
-          dst = beg;
-          for (uint32_t i = beg; i < end; ++i) dst += ii[opos[i]] < id;
+      if (loose(beg, end)) {
+        if (HG_BIN_PEND && end - beg == 2) {  // the other slot decides
+          const uint32_t o = opos[j == beg ? beg + 1 : beg];
+          dst = beg + (ANY ? (uint32_t)(ii[o] < id) : (uint32_t)(o < p));
+        } else if (HG_BIN_PEND) {
+          const uint32_t k = atomicAdd(&nheavy[1], 1u);
+          if (k < pend_cap) {
+            pend[k] = (uint16_t)j;
+            continue;
+          }
+          dst = rank_of(beg, end, p, id);
+        } else {
+          dst = rank_of(beg, end, p, id);
         }
-      } else if (end - beg > 1 && end - beg <= kBinSmallBucket) {
-        dst = beg;
-        for (uint32_t i = beg; i < end; ++i) dst += opos[i] < p;
       }
       a.csr_k[start + dst] = key;
       a.csr_i[start + dst] = map.out_id(id);
+    }
+    if (HG_BIN_PEND) {
+      __syncthreads();
+      const uint32_t np = min(nheavy[1], pend_cap);
+      for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
+        const uint32_t j = pend[k];
+        const uint32_t p = opos[j];
+        const K key = kk[p];
+        const uint32_t id = ii[p];
+        const uint32_t l = LB ? (uint32_t)lb[p] : map(key, id) - (uint32_t)bucket0;
+        const uint32_t end = (cnt[l >> 1] >> ((l & 1u) << 4)) & 0xffffu;
+        const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
+        const uint32_t dst = rank_of(beg, end, p, id);
+        a.csr_k[start + dst] = key;
+        a.csr_i[start + dst] = map.out_id(id);
+      }
     }
     for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
       const uint32_t first = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
@@ -1647,80 +1702,80 @@ __global__ void k_scatter_counts(const uint32_t* __restrict__ Qi, const uint32_t
 constexpr int kUnpermuteThreads = 1024;
 constexpr uint32_t kUnpermuteTile = HG_UNPERMUTE_TILE;  // outputs per merge tile (shared memory: 4 B each)
 
-// Every warp merges the groups warp, warp + 32, ... (GPW of them); per round
-// it loads UNR runs of 32 (position, count) pairs of each of its groups, so
-// GPW * UNR pairs per lane are in flight (eight for any number of groups).
-template <int GPW, int UNR>
-__global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t* __restrict__ Qi,
-                                                                 const uint32_t* __restrict__ Qc,
-                                                                 const uint32_t* __restrict__ GS, uint32_t ng,
-                                                                 uint64_t Q, uint64_t span,
-                                                                 uint32_t* __restrict__ counts) {
-  __shared__ uint32_t cur[256], gend[256];
+// Counts back to query order, balanced over the warps whatever the group
+// sizes (a skewed bucket map can put half of the queries into one group).
+// For every output tile [o0, o1) the run of each group (its elements with
+// positions in the tile, contiguous in its arrays) has the length the query
+// partition recorded for the partition tiles that make up the output tile
+// (TC: ng 16-bit counts per partition tile of ptile queries).  The runs,
+// back to back, are split evenly over the warps; each lane keeps
+// kUnpermuteUNR (position, count) pairs in flight and scatters them into the
+// tile in shared memory, which is then written out coalesced.
+constexpr int kUnpermuteUNR = 4;
+__global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute_bal(
+    const uint32_t* __restrict__ Qi, const uint32_t* __restrict__ Qc, const uint32_t* __restrict__ GS, uint32_t ng,
+    const uint16_t* __restrict__ TC, uint32_t ptile, uint64_t Q, uint64_t span, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t cur[256], run[256], rstart[257], wsum[32];
   extern __shared__ uint32_t out_s[];  // kUnpermuteTile entries
   const uint64_t ob = (uint64_t)blockIdx.x * span;
   if (ob >= Q) return;
   const uint64_t oe = min(ob + span, Q);
   if (threadIdx.x < ng) {  // first query of each group at or after ob
     uint32_t lo = GS[threadIdx.x], hi = GS[threadIdx.x + 1];
-    gend[threadIdx.x] = hi;
     while (lo < hi) {
       const uint32_t mid = lo + ((hi - lo) >> 1);
       if (Qi[mid] < ob) lo = mid + 1; else hi = mid;
     }
     cur[threadIdx.x] = lo;
   }
-  __syncthreads();
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint64_t o0 = ob; o0 < oe; o0 += kUnpermuteTile) {
     const uint64_t o1 = min(o0 + (uint64_t)kUnpermuteTile, oe);
-    uint32_t c[GPW], e[GPW];
-    bool act[GPW];
-#pragma unroll
-    for (int k = 0; k < GPW; ++k) {
-      const uint32_t g = warp + k * nw;
-      act[k] = g < ng;
-      c[k] = act[k] ? cur[g] : 0u;
-      e[k] = act[k] ? gend[g] : 0u;
+    const uint32_t total = (uint32_t)(o1 - o0);
+    // 1. every group's run in this tile, and where it starts among all runs
+    uint32_t r = 0;
+    if (threadIdx.x < ng)
+      for (uint64_t t = o0 / ptile; t * ptile < o1; ++t) r += TC[t * ng + threadIdx.x];
+    const uint32_t st = block_excl_scan<uint32_t>(r, wsum, (uint32_t*)nullptr);
+    if (threadIdx.x < ng) {
+      run[threadIdx.x] = r;
+      rstart[threadIdx.x] = st;
     }
-    bool any = true;
-    while (any) {
-      uint32_t v[GPW][UNR], x[GPW][UNR];
+    if (threadIdx.x == 0) rstart[ng] = total;
+    __syncthreads();
+    // 2. the runs back to back, an equal slice per warp
+    const uint32_t per = (total + nw - 1) / nw;
+    const uint32_t x0 = min(warp * per, total), x1 = min(x0 + per, total);
+    uint32_t g = 0;  // last group whose run starts at or before x0
+    {
+      uint32_t lo = 0, hi = ng;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (rstart[mid] <= x0) lo = mid; else hi = mid;
+      }
+      g = lo;
+    }
+    for (uint32_t xb = x0; xb < x1; xb += 32u * kUnpermuteUNR) {
+      uint32_t v[kUnpermuteUNR], c[kUnpermuteUNR];
 #pragma unroll
-      for (int k = 0; k < GPW; ++k) {
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          v[k][u] = 0xffffffffu;
-          x[k][u] = 0u;
-          const uint32_t j = c[k] + 32u * u + lane;
-          if (act[k] && j < e[k]) {
-            v[k][u] = __ldcs(Qi + j);
-            x[k][u] = __ldcs(Qc + j);
-          }
+      for (int u = 0; u < kUnpermuteUNR; ++u) {
+        const uint32_t x = xb + 32u * u + lane;
+        v[u] = 0xffffffffu;
+        c[u] = 0u;
+        if (x < x1) {
+          while (rstart[g + 1] <= x) ++g;
+          const uint32_t j = cur[g] + (x - rstart[g]);
+          v[u] = __ldcs(Qi + j);
+          c[u] = __ldcs(Qc + j);
         }
       }
-      any = false;
 #pragma unroll
-      for (int k = 0; k < GPW; ++k) {
-#pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          if (!act[k]) break;  // warp-uniform
-          const bool in = (uint64_t)v[k][u] < o1;
-          if (in) out_s[v[k][u] - (uint32_t)o0] = x[k][u];
-          const uint32_t n = __popc(__ballot_sync(kFull, in));
-          c[k] += n;
-          act[k] = n == 32;
-        }
-        any |= act[k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < GPW; ++k) {
-      const uint32_t g = warp + k * nw;
-      if (g < ng && lane == 0) cur[g] = c[k];
+      for (int u = 0; u < kUnpermuteUNR; ++u)
+        if (v[u] != 0xffffffffu) out_s[v[u] - (uint32_t)o0] = c[u];
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < (uint32_t)(o1 - o0); t += blockDim.x) __stcs(counts + o0 + t, out_s[t]);
+    if (threadIdx.x < ng) cur[threadIdx.x] += run[threadIdx.x];
+    for (uint32_t t = threadIdx.x; t < total; t += blockDim.x) __stcs(counts + o0 + t, out_s[t]);
     __syncthreads();
   }
 }
@@ -1736,6 +1791,12 @@ constexpr uint64_t kQueryBlock = 4096;
 static_assert(kQueryBlock % (kPartNW * 32 * part_ipt_queries<uint32_t>()) == 0 &&
                   kQueryBlock % (kPartNW * 32 * part_ipt_queries<uint64_t>()) == 0 && kUnpermuteTile % kQueryBlock == 0,
               "query blocks are whole partition tiles; merge tiles are whole blocks");
+
+// Elements per tile of the query partition (whole tiles per query block).
+static uint32_t query_tile(int kb) {
+  return kb == 8 ? (uint32_t)(kPartNW * 32 * part_ipt_queries<uint64_t>())
+                 : (uint32_t)(kPartNW * 32 * part_ipt_queries<uint32_t>());
+}
 
 #ifndef HG_PROBE_GROUP_BITS
 #define HG_PROBE_GROUP_BITS 7  // log2 of the query groups (at most 8; 7 measured best at 2^28)
@@ -1770,6 +1831,8 @@ bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePl
   p->o_qk = o;  o = align_up(o + ((size_t)q + 16) * kb);
   p->o_qi = o;  o = align_up(o + ((size_t)q + 16) * 4);
   p->o_qc = o;  o = align_up(o + ((size_t)q + 16) * 4);
+  p->ptile = query_tile(kb);
+  p->o_tc = o;  o = align_up(o + ((size_t)(q + p->ptile - 1) / p->ptile) * p->ng * 2);
   p->total = o;
   return true;
 }
@@ -1822,6 +1885,7 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.CT = CT;
   pa.BS = GS;
   pa.status = &hdr->status;
+  pa.tile_counts = Map::kNeedsPos ? nullptr : (uint16_t*)(ws + p.o_tc);
   {
     const size_t own = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW);
     pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
@@ -1845,15 +1909,9 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
       k_scatter_counts<<<(unsigned)std::min<uint64_t>((q + 255) / 256, (uint64_t)di.sms * 16), 256, 0, st>>>(
           qi, qc, q, counts);
     else {
-      auto launch = [&](auto kern) {
-        set_smem_once(kern, (size_t)kUnpermuteTile * 4);
-        kern<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.ng, q, span,
-                                                                                    counts);
-      };
-      if (p.ng <= 32) launch(k_unpermute<1, 8>);
-      else if (p.ng <= 64) launch(k_unpermute<2, 4>);
-      else if (p.ng <= 128) launch(k_unpermute<4, 2>);
-      else launch(k_unpermute<8, 1>);
+      set_smem_once(k_unpermute_bal, (size_t)kUnpermuteTile * 4);
+      k_unpermute_bal<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(
+          qi, qc, GS, p.ng, (const uint16_t*)(ws + p.o_tc), p.ptile, q, span, counts);
     }
   }
   return last_launch_status();
@@ -1887,6 +1945,8 @@ bool make_slab_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, Sl
   p->o_qk = o;  o = align_up(o + ((size_t)q + 16) * kb);
   p->o_qi = o;  o = align_up(o + ((size_t)q + 16) * 4);
   p->o_qc = o;  o = align_up(o + ((size_t)q + 16) * 4);
+  p->ptile = query_tile(kb);
+  p->o_tc = o;  o = align_up(o + ((size_t)(q + p->ptile - 1) / p->ptile) * p->S * 2);
   p->o_sub = o; o = align_up(o + p->sub.total);
   p->total = o;
   return true;
@@ -1936,6 +1996,7 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
     pa.CT = CT;
     pa.BS = GS;
     pa.status = &hdr->status;
+    pa.tile_counts = (uint16_t*)(ws + p.o_tc);
     const size_t own = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW);
     pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
     auto kern = k_partition<K, Map, false, part_ipt_queries<K>(), kPartNW, kPartMinBlocksQ, true>;
@@ -1969,10 +2030,10 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
     const uint64_t blocks = (q + kQueryBlock - 1) / kQueryBlock;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)2 * di.sms));
     const uint64_t span = (blocks + grid - 1) / grid * kQueryBlock;
-    auto kern = k_unpermute<1, 8>;
-    set_smem_once(kern, (size_t)kUnpermuteTile * 4);
+    set_smem_once(k_unpermute_bal, (size_t)kUnpermuteTile * 4);
     HG_TRACE("k_unpermute", st);
-    kern<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.S, q, span, counts);
+    k_unpermute_bal<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(
+        qi, qc, GS, p.S, (const uint16_t*)(ws + p.o_tc), p.ptile, q, span, counts);
   }
   return last_launch_status();
 }

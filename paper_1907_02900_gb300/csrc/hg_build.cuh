@@ -138,7 +138,8 @@ struct ProbePlan {
   uint32_t ng;   // groups (<= 256)
   uint32_t G;    // query chunks
   uint64_t chunk;
-  size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, total;
+  uint32_t ptile;  // queries per tile of the query partition
+  size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, o_tc, total;
 };
 bool make_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, ProbePlan* p);
 // Binned probe of a table of more than 2^kSlabProbeLog2 buckets: 128 query
@@ -153,8 +154,9 @@ struct SlabProbePlan {
   uint64_t V, q;
   uint32_t Ls, S, G;
   uint64_t chunk;
+  uint32_t ptile;
   ProbePlan sub;  // plan of a slab holding all q queries: the bound of every slab probe's workspace
-  size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, o_sub, total;
+  size_t o_H, o_C, o_CT, o_GS, o_ovf, o_qk, o_qi, o_qc, o_tc, o_sub, total;
 };
 bool make_slab_probe_plan(const hg_config* cfg, uint64_t table_n, uint64_t q, SlabProbePlan* p);
 template <typename K, typename Map>

@@ -156,12 +156,14 @@ __device__ __forceinline__ void tile_partition_fast(const K (&key)[IPT], const u
 // Used only where the bin build restores the canonical order by id.
 // Preconditions: tcnt[0 .. 256) is zero; ndig <= blockDim.x.  IMPLICIT as
 // for tile_partition_fast.
+// tile_counts (optional): receives the tile's count of every digit (16-bit).
 template <typename K, int IPT, int NW, bool IMPLICIT>
 __device__ __forceinline__ void tile_partition_any(const K (&key)[IPT], const uint32_t (&val)[IPT],
                                                    const uint32_t (&dig)[IPT], uint32_t n, int ndig, K* sk,
                                                    uint32_t* sv, uint8_t* sd, uint32_t* tcnt, uint32_t* delta,
                                                    uint32_t* cursor, uint32_t* wsum, K* __restrict__ out_k,
-                                                   uint32_t* __restrict__ out_v, uint32_t id_base) {
+                                                   uint32_t* __restrict__ out_v, uint32_t id_base,
+                                                   uint16_t* __restrict__ tile_counts = nullptr) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t seg0 = (uint32_t)w * (32u * IPT);
   uint32_t rank[IPT];
@@ -173,6 +175,7 @@ __device__ __forceinline__ void tile_partition_any(const K (&key)[IPT], const ui
   __syncthreads();
   const int t = threadIdx.x;
   const uint32_t tot = t < ndig ? tcnt[t] : 0u;
+  if (tile_counts != nullptr && t < ndig) tile_counts[t] = (uint16_t)tot;
   const uint32_t start = block_excl_scan_nt<uint32_t>(tot, wsum);
   if (t < ndig) {
     tcnt[t] = start;
