@@ -499,6 +499,18 @@ def run_scale(c: Ctx):
         for i in range(args.e2e_slots):   # warm-up of every slot
             host_step(i)
         torch.cuda.synchronize()
+        # the host link's own copy rates on this machine (pinned buffers, one copy
+        # each way of the keys), which bound the end-to-end rate
+        link = {}
+        for name, dst, src in (("h2d_gbs", slots[0]["dk"].view(torch.int32), keys_p),
+                               ("d2h_gbs", keys_p, slots[0]["dk"].view(torch.int32))):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(c.stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(c.stream)
+            torch.cuda.synchronize()
+            link[name] = round(4 * n / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1)
         c.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -518,7 +530,7 @@ def run_scale(c: Ctx):
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * (n + q), "d2h_bytes_per_step": 4 * q,
                "call": f"hg_build_probe_host, pinned host buffers, {args.e2e_slots} batches in flight",
-               "counts_returned": ok}
+               "counts_returned": ok, "host_link": link}
         del slots
 
     # Duplicate keys come from [1 .. N/D] as raw values, so a miss query (a

@@ -581,21 +581,13 @@ __device__ __forceinline__ void warp_rank_ids(uint16_t* opos, const uint32_t* ii
 #ifndef HG_ANY_WARP_RANK
 #define HG_ANY_WARP_RANK 1
 #endif
-// Slots of buckets of 3 .. 32 edges (and longer ones no warp ranked) are
-// ranked in a second, compact pass over a list of them instead of inside the
-// main write loop, where every warp would wait for its longest bucket.
-#ifndef HG_BIN_PEND
-#define HG_BIN_PEND 0
-#endif
-constexpr uint32_t kBinPendDiv = 2;  // list capacity: emax / kBinPendDiv slots (overflow ranked inline)
 
 // Shared memory of k_binbuild: staging buffers of keys and ids, the local
 // bucket array (LB), slot order (u16), packed u16 bucket counters, the list
 // of long buckets, kBinBitmapWarps position bitmaps and small control state.
 size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
   size_t b = (size_t)nbuf * (emax + 16) * (kb + 4) + (lb ? (size_t)emax * 2 : 0) + (size_t)emax * 2 +
-             (((size_t)1 << s) + 1) / 2 * 4 + ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2 +
-             (HG_BIN_PEND ? ((size_t)emax / kBinPendDiv + 2) * 2 : 0);
+             (((size_t)1 << s) + 1) / 2 * 4 + ((size_t)emax / (kBinSmallBucket + 1) + 2) * 2;
   b = align_up(b, 16) + (size_t)kBinBitmapWarps * ((emax + 31) / 32) * 4;
   return align_up(b, 16) + 32 * 4 + 16 + 2 * kMaxBinsPerCta * 4 + 2 * 8 + 64;
 }
@@ -637,15 +629,13 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
   uint16_t* opos = (uint16_t*)sp; sp += (size_t)a.emax * 2;
   uint32_t* cnt = (uint32_t*)sp; sp += (((size_t)1 << a.s) + 1) / 2 * 4;
   uint16_t* heavy = (uint16_t*)sp; sp += (size_t)(a.emax / (kBinSmallBucket + 1) + 2) * 2;
-  uint16_t* pend = (uint16_t*)sp; sp += HG_BIN_PEND ? (size_t)(a.emax / kBinPendDiv + 2) * 2 : 0;
-  const uint32_t pend_cap = a.emax / kBinPendDiv;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   const uint32_t bm_words = (a.emax + 31) / 32;
   uint32_t* bitmaps = (uint32_t*)sp;  // NBM bitmaps of bm_words words
   sp += (size_t)NBM * bm_words * 4;
   sp = (uint8_t*)(((uintptr_t)sp + 15) & ~(uintptr_t)15);
   uint32_t* wsum = (uint32_t*)sp; sp += 32 * 4;
-  uint32_t* nheavy = (uint32_t*)sp; sp += 16;  // [0] long buckets, [1] pending slots
+  uint32_t* nheavy = (uint32_t*)sp; sp += 16;
   uint32_t* bl_start = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;  // this CTA's bins: start, size
   uint32_t* bl_size = (uint32_t*)sp; sp += kMaxBinsPerCta * 4;
   uint64_t* bar = (uint64_t*)sp;
@@ -694,10 +684,7 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
     const uint32_t nb = (uint32_t)min((uint64_t)1 << a.s, a.V - bucket0);
     const uint32_t nwords = (nb + 1) >> 1;
     for (uint32_t w = threadIdx.x; w < nwords; w += blockDim.x) cnt[w] = 0;
-    if (threadIdx.x == 0) {
-      nheavy[0] = 0;
-      nheavy[1] = 0;
-    }
+    if (threadIdx.x == 0) *nheavy = 0;
     const uint32_t parity = nbuf == 2 ? (it >> 1) & 1u : it & 1u;
     if (!mbar_wait_block(&bar[buf], parity, a.status)) return;
     const uint32_t E = bl_size[jb], start = bl_start[jb];
@@ -831,40 +818,9 @@ __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map m
       const uint32_t l = LB ? (uint32_t)lb[p] : map(key, id) - (uint32_t)bucket0;
       const uint32_t end = (cnt[l >> 1] >> ((l & 1u) << 4)) & 0xffffu;
       const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
-      uint32_t dst = j;
-      if (loose(beg, end)) {
-        if (HG_BIN_PEND && end - beg == 2) {  // the other slot decides
-          const uint32_t o = opos[j == beg ? beg + 1 : beg];
-          dst = beg + (ANY ? (uint32_t)(ii[o] < id) : (uint32_t)(o < p));
-        } else if (HG_BIN_PEND) {
-          const uint32_t k = atomicAdd(&nheavy[1], 1u);
-          if (k < pend_cap) {
-            pend[k] = (uint16_t)j;
-            continue;
-          }
-          dst = rank_of(beg, end, p, id);
-        } else {
-          dst = rank_of(beg, end, p, id);
-        }
-      }
+      const uint32_t dst = loose(beg, end) ? rank_of(beg, end, p, id) : j;
       a.csr_k[start + dst] = key;
       a.csr_i[start + dst] = map.out_id(id);
-    }
-    if (HG_BIN_PEND) {
-      __syncthreads();
-      const uint32_t np = min(nheavy[1], pend_cap);
-      for (uint32_t k = threadIdx.x; k < np; k += blockDim.x) {
-        const uint32_t j = pend[k];
-        const uint32_t p = opos[j];
-        const K key = kk[p];
-        const uint32_t id = ii[p];
-        const uint32_t l = LB ? (uint32_t)lb[p] : map(key, id) - (uint32_t)bucket0;
-        const uint32_t end = (cnt[l >> 1] >> ((l & 1u) << 4)) & 0xffffu;
-        const uint32_t beg = l ? (cnt[(l - 1) >> 1] >> (((l - 1) & 1u) << 4)) & 0xffffu : 0u;
-        const uint32_t dst = rank_of(beg, end, p, id);
-        a.csr_k[start + dst] = key;
-        a.csr_i[start + dst] = map.out_id(id);
-      }
     }
     for (uint32_t v = threadIdx.x; v < nb; v += blockDim.x) {
       const uint32_t first = v ? (cnt[(v - 1) >> 1] >> (((v - 1) & 1u) << 4)) & 0xffffu : 0u;
@@ -1702,6 +1658,84 @@ __global__ void k_scatter_counts(const uint32_t* __restrict__ Qi, const uint32_t
 constexpr int kUnpermuteThreads = 1024;
 constexpr uint32_t kUnpermuteTile = HG_UNPERMUTE_TILE;  // outputs per merge tile (shared memory: 4 B each)
 
+// Every warp merges the groups warp, warp + 32, ... (GPW of them); per round
+// it loads UNR runs of 32 (position, count) pairs of each of its groups, so
+// GPW * UNR pairs per lane are in flight (eight for any number of groups).
+template <int GPW, int UNR>
+__global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute(const uint32_t* __restrict__ Qi,
+                                                                 const uint32_t* __restrict__ Qc,
+                                                                 const uint32_t* __restrict__ GS, uint32_t ng,
+                                                                 uint64_t Q, uint64_t span,
+                                                                 uint32_t* __restrict__ counts) {
+  __shared__ uint32_t cur[256], gend[256];
+  extern __shared__ uint32_t out_s[];  // kUnpermuteTile entries
+  const uint64_t ob = (uint64_t)blockIdx.x * span;
+  if (ob >= Q) return;
+  const uint64_t oe = min(ob + span, Q);
+  if (threadIdx.x < ng) {  // first query of each group at or after ob
+    uint32_t lo = GS[threadIdx.x], hi = GS[threadIdx.x + 1];
+    gend[threadIdx.x] = hi;
+    while (lo < hi) {
+      const uint32_t mid = lo + ((hi - lo) >> 1);
+      if (Qi[mid] < ob) lo = mid + 1; else hi = mid;
+    }
+    cur[threadIdx.x] = lo;
+  }
+  __syncthreads();
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint64_t o0 = ob; o0 < oe; o0 += kUnpermuteTile) {
+    const uint64_t o1 = min(o0 + (uint64_t)kUnpermuteTile, oe);
+    uint32_t c[GPW], e[GPW];
+    bool act[GPW];
+#pragma unroll
+    for (int k = 0; k < GPW; ++k) {
+      const uint32_t g = warp + k * nw;
+      act[k] = g < ng;
+      c[k] = act[k] ? cur[g] : 0u;
+      e[k] = act[k] ? gend[g] : 0u;
+    }
+    bool any = true;
+    while (any) {
+      uint32_t v[GPW][UNR], x[GPW][UNR];
+#pragma unroll
+      for (int k = 0; k < GPW; ++k) {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          v[k][u] = 0xffffffffu;
+          x[k][u] = 0u;
+          const uint32_t j = c[k] + 32u * u + lane;
+          if (act[k] && j < e[k]) {
+            v[k][u] = __ldcs(Qi + j);
+            x[k][u] = __ldcs(Qc + j);
+          }
+        }
+      }
+      any = false;
+#pragma unroll
+      for (int k = 0; k < GPW; ++k) {
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          if (!act[k]) break;  // warp-uniform
+          const bool in = (uint64_t)v[k][u] < o1;
+          if (in) out_s[v[k][u] - (uint32_t)o0] = x[k][u];
+          const uint32_t n = __popc(__ballot_sync(kFull, in));
+          c[k] += n;
+          act[k] = n == 32;
+        }
+        any |= act[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < GPW; ++k) {
+      const uint32_t g = warp + k * nw;
+      if (g < ng && lane == 0) cur[g] = c[k];
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < (uint32_t)(o1 - o0); t += blockDim.x) __stcs(counts + o0 + t, out_s[t]);
+    __syncthreads();
+  }
+}
+
 // Counts back to query order, balanced over the warps whatever the group
 // sizes (a skewed bucket map can put half of the queries into one group).
 // For every output tile [o0, o1) the run of each group (its elements with
@@ -1711,7 +1745,7 @@ constexpr uint32_t kUnpermuteTile = HG_UNPERMUTE_TILE;  // outputs per merge til
 // back to back, are split evenly over the warps; each lane keeps
 // kUnpermuteUNR (position, count) pairs in flight and scatters them into the
 // tile in shared memory, which is then written out coalesced.
-constexpr int kUnpermuteUNR = 4;
+constexpr int kUnpermuteUNR = 8;
 __global__ void __launch_bounds__(kUnpermuteThreads) k_unpermute_bal(
     const uint32_t* __restrict__ Qi, const uint32_t* __restrict__ Qc, const uint32_t* __restrict__ GS, uint32_t ng,
     const uint16_t* __restrict__ TC, uint32_t ptile, uint64_t Q, uint64_t span, uint32_t* __restrict__ counts) {
@@ -1885,7 +1919,7 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   pa.CT = CT;
   pa.BS = GS;
   pa.status = &hdr->status;
-  pa.tile_counts = Map::kNeedsPos ? nullptr : (uint16_t*)(ws + p.o_tc);
+  pa.tile_counts = Map::kSkewed ? (uint16_t*)(ws + p.o_tc) : nullptr;
   {
     const size_t own = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW);
     pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
@@ -1909,9 +1943,21 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
       k_scatter_counts<<<(unsigned)std::min<uint64_t>((q + 255) / 256, (uint64_t)di.sms * 16), 256, 0, st>>>(
           qi, qc, q, counts);
     else {
-      set_smem_once(k_unpermute_bal, (size_t)kUnpermuteTile * 4);
-      k_unpermute_bal<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(
-          qi, qc, GS, p.ng, (const uint16_t*)(ws + p.o_tc), p.ptile, q, span, counts);
+      if (Map::kSkewed) {
+        set_smem_once(k_unpermute_bal, (size_t)kUnpermuteTile * 4);
+        k_unpermute_bal<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(
+            qi, qc, GS, p.ng, (const uint16_t*)(ws + p.o_tc), p.ptile, q, span, counts);
+      } else {  // even groups: one warp per group merges faster
+        auto launch = [&](auto kern) {
+          set_smem_once(kern, (size_t)kUnpermuteTile * 4);
+          kern<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.ng, q, span,
+                                                                                      counts);
+        };
+        if (p.ng <= 32) launch(k_unpermute<1, 8>);
+        else if (p.ng <= 64) launch(k_unpermute<2, 4>);
+        else if (p.ng <= 128) launch(k_unpermute<4, 2>);
+        else launch(k_unpermute<8, 1>);
+      }
     }
   }
   return last_launch_status();
@@ -1996,7 +2042,7 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
     pa.CT = CT;
     pa.BS = GS;
     pa.status = &hdr->status;
-    pa.tile_counts = (uint16_t*)(ws + p.o_tc);
+    pa.tile_counts = Map::kSkewed ? (uint16_t*)(ws + p.o_tc) : nullptr;
     const size_t own = part_smem_bytes(sizeof(K), false, part_ipt_queries<K>(), false, kPartNW);
     pa.stage_bytes = own + Map::kStageBytes <= (size_t)di.max_smem_optin ? (uint32_t)Map::kStageBytes : 0u;
     auto kern = k_partition<K, Map, false, part_ipt_queries<K>(), kPartNW, kPartMinBlocksQ, true>;
@@ -2030,10 +2076,16 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
     const uint64_t blocks = (q + kQueryBlock - 1) / kQueryBlock;
     const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)2 * di.sms));
     const uint64_t span = (blocks + grid - 1) / grid * kQueryBlock;
-    set_smem_once(k_unpermute_bal, (size_t)kUnpermuteTile * 4);
     HG_TRACE("k_unpermute", st);
-    k_unpermute_bal<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(
-        qi, qc, GS, p.S, (const uint16_t*)(ws + p.o_tc), p.ptile, q, span, counts);
+    if (Map::kSkewed) {
+      set_smem_once(k_unpermute_bal, (size_t)kUnpermuteTile * 4);
+      k_unpermute_bal<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(
+          qi, qc, GS, p.S, (const uint16_t*)(ws + p.o_tc), p.ptile, q, span, counts);
+    } else {
+      auto kern = k_unpermute<1, 8>;
+      set_smem_once(kern, (size_t)kUnpermuteTile * 4);
+      kern<<<(unsigned)grid, kUnpermuteThreads, (size_t)kUnpermuteTile * 4, st>>>(qi, qc, GS, p.S, q, span, counts);
+    }
   }
   return last_launch_status();
 }
@@ -2045,6 +2097,7 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
 // ===========================================================================
 struct RadixByteMap {
   static constexpr bool kNeedsPos = false;
+  static constexpr bool kSkewed = false;
   static constexpr size_t kStageBytes = 0;
   uint32_t shift;
   __device__ __forceinline__ void init() {}

@@ -67,8 +67,12 @@ struct FastMod {
 // Eq. 1: bucket = hash(key) mod V.
 // slab_base: first bucket of the slab a build works on (the map returns the
 // bucket minus slab_base; 0 for a whole table).
+// kSkewed: the map may send most queries to a few buckets (an order-
+// preserving map does, with keys outside the fitted range); the probe then
+// merges its counts back with a balanced merge.
 struct MurmurMap {
   static constexpr bool kNeedsPos = false;
+  static constexpr bool kSkewed = false;
   static constexpr size_t kStageBytes = 0;  // shared memory stage() can use
   uint32_t seed;
   uint32_t slab_base;
@@ -96,6 +100,7 @@ struct MurmurMap {
 // the buckets bucket_base + [0, V).
 struct BatchedMap {
   static constexpr bool kNeedsPos = true;
+  static constexpr bool kSkewed = false;
   static constexpr size_t kStageBytes = 0;
   uint32_t seed;
   uint32_t page_shift;
@@ -105,27 +110,45 @@ struct BatchedMap {
   const uint32_t* len;    // [T] positions of each table that hold keys
   const uint32_t* page;   // table holding position (p << page_shift)
   const uint4* desc;      // per table: {global bucket base, V_t, fastmod M low, M high}
-  __device__ __forceinline__ void init() {}
+  // The table of the last lookup, kept by each thread: the elements one
+  // thread handles mostly belong to the same (large) table, so most lookups
+  // become two comparisons.  Positions relative to pos_base: [c_lo, c_hi)
+  // the table's positions, [c_lo, c_kend) those holding keys.
+  mutable uint32_t c_lo, c_hi, c_kend;
+  mutable uint4 c_d;
+  __device__ __forceinline__ void init() {
+    c_lo = 1u;
+    c_hi = 0u;  // empty: the first lookup misses
+  }
   __device__ __forceinline__ void stage(uint8_t*, size_t) {}
   __device__ __forceinline__ uint32_t table_of(uint64_t p) const {
     uint32_t t = __ldg(page + (p >> page_shift));
     while (__ldg((const unsigned long long*)begin + t + 1) <= p) ++t;
     return t;
   }
-  template <typename K>
-  __device__ __forceinline__ uint32_t operator()(K key, uint32_t pos) const {
+  __device__ __forceinline__ void lookup(uint32_t pos) const {
+    if (pos - c_lo < c_hi - c_lo) return;  // inside the cached table (also rejects the empty cache)
     const uint64_t p = pos_base + pos;
     const uint32_t t = table_of(p);
-    const uint4 d = __ldg(desc + t);
-    if (p - __ldg((const unsigned long long*)begin + t) >= __ldg(len + t)) return d.x - bucket_base + d.y;
-    const uint64_t M = ((uint64_t)d.w << 32) | d.z;
-    const uint32_t local = (uint32_t)__umul64hi(M * (uint64_t)murmur3(key, seed), (uint64_t)d.y);
-    return d.x - bucket_base + local;
+    const uint64_t b0 = __ldg((const unsigned long long*)begin + t);
+    const uint64_t b1 = __ldg((const unsigned long long*)begin + t + 1);
+    c_lo = (uint32_t)(b0 - pos_base);
+    c_hi = (uint32_t)(b1 - pos_base);
+    c_kend = c_lo + __ldg(len + t);
+    c_d = __ldg(desc + t);
+  }
+  template <typename K>
+  __device__ __forceinline__ uint32_t operator()(K key, uint32_t pos) const {
+    lookup(pos);
+    if (pos >= c_kend) return c_d.x - bucket_base + c_d.y;
+    const uint64_t M = ((uint64_t)c_d.w << 32) | c_d.z;
+    const uint32_t local = (uint32_t)__umul64hi(M * (uint64_t)murmur3(key, seed), (uint64_t)c_d.y);
+    return c_d.x - bucket_base + local;
   }
   // ids are stored table-local: position minus the table's first position
   __device__ __forceinline__ uint32_t out_id(uint32_t pos) const {
-    const uint64_t p = pos_base + pos;
-    return (uint32_t)(p - __ldg((const unsigned long long*)begin + table_of(p)));
+    lookup(pos);
+    return pos - c_lo;
   }
 };
 
@@ -162,6 +185,7 @@ constexpr uint32_t kStageLeaves = 1024;  // leaf records a kernel can stage in s
 
 struct LearnedMap {
   static constexpr bool kNeedsPos = false;
+  static constexpr bool kSkewed = true;
   static constexpr size_t kStageBytes = kStageLeaves * sizeof(LearnedLeaf);
   const uint8_t* blob;  // device pointer
   uint64_t Vcap;        // buckets of the table being built (host-provided bound)
