@@ -112,13 +112,14 @@ struct BatchedMap {
   const uint4* desc;      // per table: {global bucket base, V_t, fastmod M low, M high}
   // The table of the last lookup, kept by each thread: the elements one
   // thread handles mostly belong to the same (large) table, so most lookups
-  // become two comparisons.  Positions relative to pos_base: [c_lo, c_hi)
-  // the table's positions, [c_lo, c_kend) those holding keys.
-  mutable uint32_t c_lo, c_hi, c_kend;
+  // become one comparison.  c_lo: the table's first position relative to
+  // pos_base (modulo 2^32); c_n: its positions; c_len: those holding keys.
+  // All tests are on pos - c_lo, which stays correct when c_lo wraps.
+  mutable uint32_t c_lo, c_n, c_len;
   mutable uint4 c_d;
   __device__ __forceinline__ void init() {
-    c_lo = 1u;
-    c_hi = 0u;  // empty: the first lookup misses
+    c_lo = 0u;
+    c_n = 0u;  // empty range: the first lookup misses
   }
   __device__ __forceinline__ void stage(uint8_t*, size_t) {}
   __device__ __forceinline__ uint32_t table_of(uint64_t p) const {
@@ -127,20 +128,20 @@ struct BatchedMap {
     return t;
   }
   __device__ __forceinline__ void lookup(uint32_t pos) const {
-    if (pos - c_lo < c_hi - c_lo) return;  // inside the cached table (also rejects the empty cache)
+    if (pos - c_lo < c_n) return;  // inside the cached table
     const uint64_t p = pos_base + pos;
     const uint32_t t = table_of(p);
     const uint64_t b0 = __ldg((const unsigned long long*)begin + t);
     const uint64_t b1 = __ldg((const unsigned long long*)begin + t + 1);
     c_lo = (uint32_t)(b0 - pos_base);
-    c_hi = (uint32_t)(b1 - pos_base);
-    c_kend = c_lo + __ldg(len + t);
+    c_n = (uint32_t)(b1 - b0);
+    c_len = __ldg(len + t);
     c_d = __ldg(desc + t);
   }
   template <typename K>
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t pos) const {
     lookup(pos);
-    if (pos >= c_kend) return c_d.x - bucket_base + c_d.y;
+    if (pos - c_lo >= c_len) return c_d.x - bucket_base + c_d.y;
     const uint64_t M = ((uint64_t)c_d.w << 32) | c_d.z;
     const uint32_t local = (uint32_t)__umul64hi(M * (uint64_t)murmur3(key, seed), (uint64_t)c_d.y);
     return c_d.x - bucket_base + local;

@@ -52,13 +52,22 @@ __device__ __forceinline__ uint64_t probe_ld<uint64_t>(const uint64_t* p) {
 // twice.)  Each thread loads its next query one sweep ahead, so the query's
 // DRAM latency is not on its chain of dependent loads.  The kernel is bound
 // by L1 request throughput: a warp's random loads touch 32 sectors each.
+#ifndef HG_PROBE_VEC
+#define HG_PROBE_VEC 0
+#endif
+
 template <typename K, typename Map>
 __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q, uint64_t nq,
                                                          const uint32_t* __restrict__ off,
                                                          const K* __restrict__ ck,
                                                          uint32_t* __restrict__ out, uint32_t nquads,
-                                                         const uint32_t* __restrict__ qpos, Map map) {
+                                                         const uint32_t* __restrict__ qpos, Map map,
+                                                         uint64_t map_buckets) {
   map.init();
+#if HG_PROBE_VEC
+  // last offset of the table (0 switches the piecewise loads off: keys not 16-byte aligned)
+  const uint32_t vec_end = ((uintptr_t)ck % 16 == 0) ? __ldg(off + map_buckets) : 0u;
+#endif
   const uint64_t bd = blockDim.x;
   const uint64_t span = (uint64_t)gridDim.x * bd;
   uint64_t base = (uint64_t)blockIdx.x * bd;
@@ -83,6 +92,25 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
       e = probe_ld(off + b + 1);
     }
     uint32_t cnt = 0;
+#if HG_PROBE_VEC
+    if (s < e && vec_end != 0) {
+      // The bucket's keys in aligned 16-byte pieces: a bucket of up to 16/kb
+      // keys usually costs one load request instead of one per key.  A piece
+      // that reaches past the bucket is read only while it stays inside the
+      // table's last offset (vec_end), so no load leaves the keys array.
+      constexpr uint32_t EPQ = 16 / sizeof(K);
+      for (uint32_t j = s & ~(EPQ - 1); j < e; j += EPQ) {
+        if (j + EPQ <= vec_end) {
+          const uint4 v = probe_ld(reinterpret_cast<const uint4*>(ck + j));
+          const K* kv = reinterpret_cast<const K*>(&v);
+#pragma unroll
+          for (uint32_t l = 0; l < EPQ; ++l) cnt += (j + l >= s) & (j + l < e) & (kv[l] == key);
+        } else {
+          for (uint32_t l = max(j, s); l < e; ++l) cnt += probe_ld(ck + l) == key;
+        }
+      }
+    } else
+#endif
     if (s < e) {
       cnt = probe_ld(ck + s) == key;
       uint32_t j = s + 1;
@@ -115,7 +143,7 @@ hg_status probe_launch(const K* q, uint64_t nq, const uint32_t* off, const K* ck
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)sms * per_sm));
   {
     HG_TRACE("k_probe", st);
-    kern<<<grid, kProbeThreads, 0, st>>>(q, nq, off, ck, out, nquads, qpos, map);
+    kern<<<grid, kProbeThreads, 0, st>>>(q, nq, off, ck, out, nquads, qpos, map, V);
   }
   return last_launch_status();
 }
