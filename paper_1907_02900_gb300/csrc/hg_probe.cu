@@ -52,8 +52,10 @@ __device__ __forceinline__ uint64_t probe_ld<uint64_t>(const uint64_t* p) {
 // twice.)  Each thread loads its next query one sweep ahead, so the query's
 // DRAM latency is not on its chain of dependent loads.  The kernel is bound
 // by L1 request throughput: a warp's random loads touch 32 sectors each.
+// Bucket keys read in aligned 16-byte pieces (4-byte keys only: with 8-byte
+// keys a piece holds two and measured no faster).  0 switches it off.
 #ifndef HG_PROBE_VEC
-#define HG_PROBE_VEC 0
+#define HG_PROBE_VEC 1
 #endif
 
 template <typename K, typename Map>
@@ -64,10 +66,9 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
                                                          const uint32_t* __restrict__ qpos, Map map,
                                                          uint64_t map_buckets) {
   map.init();
-#if HG_PROBE_VEC
+  constexpr bool kVec = HG_PROBE_VEC && sizeof(K) == 4;
   // last offset of the table (0 switches the piecewise loads off: keys not 16-byte aligned)
-  const uint32_t vec_end = ((uintptr_t)ck % 16 == 0) ? __ldg(off + map_buckets) : 0u;
-#endif
+  const uint32_t vec_end = (kVec && (uintptr_t)ck % 16 == 0) ? __ldg(off + map_buckets) : 0u;
   const uint64_t bd = blockDim.x;
   const uint64_t span = (uint64_t)gridDim.x * bd;
   uint64_t base = (uint64_t)blockIdx.x * bd;
@@ -92,8 +93,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
       e = probe_ld(off + b + 1);
     }
     uint32_t cnt = 0;
-#if HG_PROBE_VEC
-    if (s < e && vec_end != 0) {
+    if (kVec && s < e && vec_end != 0) {
       // The bucket's keys in aligned 16-byte pieces: a bucket of up to 16/kb
       // keys usually costs one load request instead of one per key.  A piece
       // that reaches past the bucket is read only while it stays inside the
@@ -109,9 +109,7 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(const K* __restrict__ q
           for (uint32_t l = max(j, s); l < e; ++l) cnt += probe_ld(ck + l) == key;
         }
       }
-    } else
-#endif
-    if (s < e) {
+    } else if (s < e) {
       cnt = probe_ld(ck + s) == key;
       uint32_t j = s + 1;
       // four independent loads in flight per round for long buckets
