@@ -71,6 +71,8 @@ def parse():
                     help="scale/plain: keys drawn uniformly from [1 .. N/D], D appearances per key on average "
                          "(the duplicate-key experiment); 0 = distinct-looking uniform keys")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned-join", action="store_true",
+                    help="learned workload: skip the learned vs murmur3 join of the key and query tables")
     ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
     ap.add_argument("--cpu-mt-log2n", type=int, default=24,
                     help="sample size of the multithreaded CPU HashGraph (log2 keys); 0 = skip it")
@@ -213,9 +215,9 @@ def algo_probe(kb: int, n: int, V: int, q: int, hit: float, binned: bool = True,
 
 def algo_join(kb: int, nA: int, nB: int, V: int, M: int) -> dict:
     return {
-        "k_join_elem": kb * nA + kb * nB + 8 * (V + 1) + 8 * nA,          # both key arrays, both offsets, m out
-        "k_join_write": (kb + 4) * (nA + nB) + 4 * (V + 1) + 8 * nA + 16 * M,  # keys + ids, offsets, m, pairs
-        "k_join_bucket": 4 * (V + 1) + 8 * nA + 8 * V,
+        # both key arrays, both offsets, m out, per-bucket counts out
+        "k_join_merge": kb * nA + kb * nB + 8 * (V + 1) + 8 * nA + 8 * V,
+        "k_join_write": (kb + 4) * (nA + nB) + 8 * (V + 1) + 8 * nA + 16 * M,  # keys + ids, offsets, m, pairs
     }
 
 
@@ -617,7 +619,7 @@ def run_join(c: Ctx):
     # two builds per step
     algo = {k: 2 * v for k, v in algo_build(8, n, V).items()}
     algo.update(algo_join(8, n, n, V, M))
-    units = {k: 2 * n if k in algo_build(8, 1, 1) or k == "k_join_elem" else n for k in algo}
+    units = {k: 2 * n if k in algo_build(8, 1, 1) or k == "k_join_merge" else n for k in algo}
     roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
     join_ms = sum(prof[k][0] for k in prof if k.startswith("k_join") or k.startswith("k_scan")) / args.steps
     cpu = None
@@ -713,6 +715,59 @@ def run_batched(c: Ctx):
                   gpu_launches=sum(v[1] for v in prof.values()) * args.steps, clocks=clocks)
 
 
+def learned_joins(c: Ctx, keys_d, q_d, V: int, model) -> dict:
+    """Alg. 3 join of the key table with a table of the queries, both built
+    with the learned map and both with murmur3: count + materialise, timed
+    alone (the tables are built before the timed region).  The pair sets
+    must be equal (their order follows each map's buckets)."""
+    torch, hg, args = c.torch, c.hg, c.args
+    out = {}
+    pairs = {}
+    for name, mdl in (("learned", model), ("murmur", None)):
+        cfg = hg.make_config(hg.KEY_U64, V, 0, "v2", model=mdl)
+        tabs = []
+        for src in (keys_d, q_d):
+            n = src.numel()
+            ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=c.dev)
+            t = hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=c.dev),
+                         torch.empty(n, dtype=torch.uint64, device=c.dev),
+                         torch.empty(n, dtype=torch.uint32, device=c.dev), cfg, model=mdl)
+            hg.build_into(cfg, src, None, t.offsets, t.keys, t.ids, ws, c.stream)
+            c.torch.cuda.synchronize()
+            c.check_ws(ws, name + " join build")
+            del ws
+            tabs.append(t)
+        tA, tB = tabs
+        jws = torch.empty(hg.join_workspace_size(cfg, tA.keys.numel(), tB.keys.numel()), dtype=torch.uint8,
+                          device=c.dev)
+        total = torch.empty(1, dtype=torch.int64, device=c.dev)
+        hg.join_count_into(tA, tB, total, None, jws, c.stream)
+        M = int(total.item())
+        oa = torch.empty(max(M, 1), dtype=torch.int64, device=c.dev)
+        ob = torch.empty(max(M, 1), dtype=torch.int64, device=c.dev)
+
+        def step():
+            hg.join_count_into(tA, tB, total, None, jws, c.stream)
+            hg.join_materialize_into(tA, tB, oa, ob, total, jws, c.stream, after_count=True)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        c.check_ws(jws, name + " join")
+        el, _, prof = c.timed(step, args.steps)
+        ms = el / args.steps
+        pairs[name] = torch.sort((oa[:M] << 32) | ob[:M])[0]
+        out[name + "_ms"] = round(ms, 4)
+        out[name + "_phases_avg_ms"] = {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items()}
+        out["pairs"] = M
+        del tabs, tA, tB, jws, oa, ob
+    out["learned_vs_murmur"] = round(out["murmur_ms"] / out["learned_ms"], 3)
+    out["identical_pairs"] = bool(torch.equal(pairs["learned"], pairs["murmur"]))
+    out["workload"] = ("join of the key table with a table of the 2^27 queries (V = 2^27 each), count + "
+                       "materialise; tables built before the timed region")
+    return out
+
+
 def run_learned(c: Ctx):
     torch, hg, args = c.torch, c.hg, c.args
     from paper_1907_02900_gb300 import datagen as dg
@@ -764,6 +819,7 @@ def run_learned(c: Ctx):
         res[name] = (el, clocks, prof, counts.clone())
         del ws, pws
     same_counts = bool(torch.equal(res["learned"][3], res["murmur"][3]))
+    joins = learned_joins(c, keys_d, q_d, V, model) if not args.no_learned_join else None
     el, clocks, prof, _ = res["learned"]
     value, el_max = c.rate((n + q) * args.steps, el)
     ms = el_max / args.steps
@@ -795,7 +851,7 @@ def run_learned(c: Ctx):
                   murmur_phases_avg_ms=murmur_phases,
                   learned_vs_murmur=round(value / murmur_value, 3), identical_counts=same_counts,
                   train_ms=round(train_ms, 2), loss_before=diag["loss_before"], loss_after=diag["loss_after"],
-                  bucket_stats=rep, fallback_to_murmur=not rep["kept"], roofline=roof, phases=phases,
+                  bucket_stats=rep, fallback_to_murmur=not rep["kept"], join=joins, roofline=roof, phases=phases,
                   cpu_baseline=cpu, e2e=None, gpu_launches=sum(v[1] for v in prof.values()), clocks=clocks)
 
 

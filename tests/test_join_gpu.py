@@ -16,7 +16,7 @@ def _tables(hg, orc, a, b, V, seed=0):
     return tA, tB, rA, rB
 
 
-@pytest.mark.parametrize("V", [1, 64, 4096, 1 << 17])
+@pytest.mark.parametrize("V", [1, 64, 4096, 1 << 17, 1 << 22])
 def test_join_count_u32(hg, orc, V):
     a = dg.dup_keys_u32(120_000, 3, 1)
     b = dg.dup_keys_u32(90_000, 2, 2)
