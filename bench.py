@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned-join", action="store_true",
                     help="learned workload: skip the learned vs murmur3 join of the key and query tables")
-    ap.add_argument("--cpu-log2n", type=int, default=22, help="oracle sample size (log2 keys)")
+    ap.add_argument("--cpu-log2n", type=int, default=25, help="oracle sample size (log2 keys; 2^25 is about 10 s of CPU work)")
     ap.add_argument("--cpu-mt-log2n", type=int, default=24,
                     help="sample size of the multithreaded CPU HashGraph (log2 keys); 0 = skip it")
     ap.add_argument("--plain-steps", type=int, default=2, help="batched: timed runs of the per-table loop")
