@@ -194,29 +194,43 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const K* __restrict__ key
 }
 
 // Exclusive prefix down every column of a rows x cols table, in place;
-// column totals to coltot.
-__global__ void k_colscan(uint32_t* __restrict__ tab, uint32_t rows, uint32_t cols,
-                          uint32_t* __restrict__ coltot) {
-  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
+// column totals to coltot (may be null).  A CTA takes 32 consecutive columns
+// (lane = column) and splits the rows into 32 segments (warp = segment), so
+// every row access of a warp is one coalesced 128-byte line: segment sums,
+// a scan of each column's 32 segment sums, then the segment rewritten with
+// its prefix.  Launch with colscan_launch().
+constexpr int kColScanThreads = 1024;
+__global__ void __launch_bounds__(kColScanThreads) k_colscan(uint32_t* __restrict__ tab, uint32_t rows,
+                                                             uint32_t cols, uint32_t* __restrict__ coltot) {
+  __shared__ uint32_t seg[32][33];
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  const uint32_t c = blockIdx.x * 32u + lane;
+  const uint32_t R = (rows + 31u) / 32u;
+  const uint32_t r0 = min(w * R, rows), r1 = min(r0 + R, rows);
   uint32_t* p = tab + c;
-  uint32_t run = 0, g = 0;
-  for (; g + 8 <= rows; g += 8) {
-    uint32_t v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = p[(uint64_t)(g + u) * cols];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      p[(uint64_t)(g + u) * cols] = run;
-      run += v[u];
-    }
+  uint32_t sum = 0;
+  if (c < cols)
+    for (uint32_t r = r0; r < r1; ++r) sum += p[(uint64_t)r * cols];
+  seg[w][lane] = sum;
+  __syncthreads();
+  {  // warp w scans column w's 32 segment sums (lane = segment)
+    const uint32_t v = seg[lane][w];
+    const uint32_t incl = warp_incl_scan(v);
+    seg[lane][w] = incl - v;
   }
-  for (; g < rows; ++g) {
-    const uint32_t v = p[(uint64_t)g * cols];
-    p[(uint64_t)g * cols] = run;
+  __syncthreads();
+  if (c >= cols) return;
+  uint32_t run = seg[w][lane];
+  for (uint32_t r = r0; r < r1; ++r) {
+    const uint32_t v = p[(uint64_t)r * cols];
+    p[(uint64_t)r * cols] = run;
     run += v;
   }
-  if (coltot) coltot[c] = run;
+  if (coltot && w == 31) coltot[c] = run;
+}
+
+static void colscan_launch(uint32_t* tab, uint32_t rows, uint32_t cols, uint32_t* coltot, cudaStream_t st) {
+  k_colscan<<<(cols + 31) / 32, kColScanThreads, 0, st>>>(tab, rows, cols, coltot);
 }
 
 // Bins above kHugeSeg edges: list entries (bin, first row, rows) and one
@@ -239,39 +253,59 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ ovf_count,
                                                     uint32_t* __restrict__ offsets, uint64_t V,
                                                     uint32_t n_end, HugeArgs h, uint32_t* order) {
-  __shared__ uint32_t wsum[32];
-  const uint32_t per = (nbins + blockDim.x - 1) / blockDim.x;
-  const uint32_t b = threadIdx.x * per, e = min(b + per, nbins);
-  uint32_t s = 0;
-  for (uint32_t i = b; i < e; ++i) s += T[i];
-  uint32_t total;
-  uint32_t base = block_excl_scan<uint32_t>(s, wsum, &total);
-  for (uint32_t i = b; i < e; ++i) {
-    BS[i] = base;
-    base += T[i];
-    if (T[i] <= emax) continue;
+  // Each warp scans a contiguous range of whole 32-bin rows (lane = bin of
+  // the row), so every access is coalesced: the range's sum, an exclusive
+  // scan of the warp sums, then the range again from its base.
+  __shared__ uint32_t wbase[32];
+  __shared__ uint32_t wtotal;
+  const uint32_t lane = threadIdx.x & 31u, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t rows = (nbins + 31u) / 32u, per = (rows + nw - 1) / nw;
+  const uint32_t row0 = min(w * per, rows), row1 = min(row0 + per, rows);
+  uint32_t part = 0;
+  for (uint32_t r = row0; r < row1; ++r) {
+    const uint32_t i = r * 32u + lane;
+    part += i < nbins ? T[i] : 0u;
+  }
+  part = warp_sum(part);
+  if (lane == 0) wbase[w] = part;
+  __syncthreads();
+  if (w == 0) {
+    const uint32_t v = lane < nw ? wbase[lane] : 0u;
+    const uint32_t incl = warp_incl_scan(v);
+    if (lane < nw) wbase[lane] = incl - v;
+    if (lane == 31) wtotal = incl;
+  }
+  __syncthreads();
+  uint32_t base = wbase[w];
+  for (uint32_t r = row0; r < row1; ++r) {
+    const uint32_t i = r * 32u + lane;
+    const uint32_t t = i < nbins ? T[i] : 0u;
+    const uint32_t incl = warp_incl_scan(t);
+    if (i < nbins) BS[i] = base + incl - t;
+    base += __shfl_sync(kFull, incl, 31);
+    if (i >= nbins || t <= emax) continue;
     if (order) *order = 1u;  // this bin is built outside shared memory: stable partitions needed
-    if (h.list == nullptr || T[i] <= kHugeSeg) {
+    if (h.list == nullptr || t <= kHugeSeg) {
       ovf_list[atomicAdd(ovf_count, 1u)] = i;
       continue;
     }
-    const uint32_t nr = (T[i] + kHugeSeg - 1) / kHugeSeg;
-    const uint32_t r0 = atomicAdd(h.rows, nr);
-    if (r0 + nr > h.max_rows) {  // cannot happen: the bound counts every huge bin
+    const uint32_t nr = (t + kHugeSeg - 1) / kHugeSeg;
+    const uint32_t q0 = atomicAdd(h.rows, nr);
+    if (q0 + nr > h.max_rows) {  // cannot happen: the bound counts every huge bin
       set_status(h.status, HG_ERR_OVERFLOW);
       continue;
     }
     const uint32_t k = atomicAdd(h.count, 1u);
     h.list[3 * k] = i;
-    h.list[3 * k + 1] = r0;
+    h.list[3 * k + 1] = q0;
     h.list[3 * k + 2] = nr;
-    for (uint32_t r = 0; r < nr; ++r) {
-      h.rowdesc[2 * (r0 + r)] = i;
-      h.rowdesc[2 * (r0 + r) + 1] = r;
+    for (uint32_t x = 0; x < nr; ++x) {
+      h.rowdesc[2 * (q0 + x)] = i;
+      h.rowdesc[2 * (q0 + x) + 1] = x;
     }
   }
   if (threadIdx.x == 0) {
-    BS[nbins] = total;
+    BS[nbins] = wtotal;
     offsets[V] = n_end;
   }
 }
@@ -1249,11 +1283,11 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   }
   {
     HG_TRACE("k_colscan", st);
-    k_colscan<<<(p.nbins + 255) / 256, 256, 0, st>>>(H, p.G, p.nbins, T);
+    colscan_launch(H, p.G, p.nbins, T, st);
   }
   {
     HG_TRACE("k_colscan", st);
-    k_colscan<<<(p.nsb + 255) / 256, 256, 0, st>>>(C, p.G, p.nsb, CT);
+    colscan_launch(C, p.G, p.nsb, CT, st);
   }
   const bool two = p.sshift > 0;
   const BinCfg bc = bin_config(p, recompute_bucket<Map>::value);
@@ -1510,8 +1544,8 @@ hg_status build_slabs(const hg_config* cfg, const SlabPlan& p, const K* keys, co
     HG_TRACE("k_hist_slab", st);
     kern<<<p.G, kHistThreads, sm, st>>>(keys, p.n, p.chunk, p.Ls, p.S, 0, p.S, H, C, map,
                                         (uint32_t)Map::kStageBytes);
-    k_colscan<<<1, 256, 0, st>>>(H, p.G, p.S, T);
-    k_colscan<<<1, 256, 0, st>>>(C, p.G, p.S, CT);
+    colscan_launch(H, p.G, p.S, T, st);
+    colscan_launch(C, p.G, p.S, CT, st);
     k_scan_bins<<<1, 1024, 0, st>>>(T, p.S, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.S, 0, (uint32_t)p.n,
                                     HugeArgs{}, nullptr);
   }
@@ -1894,7 +1928,7 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
   }
   {
     HG_TRACE("k_colscan_Q", st);
-    k_colscan<<<(p.ng + 255) / 256, 256, 0, st>>>(C, p.G, p.ng, CT);
+    colscan_launch(C, p.G, p.ng, CT, st);
   }
   {
     HG_TRACE("k_scan_Q", st);
@@ -2020,7 +2054,7 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
     HG_TRACE("k_hist_Q", st);
     kern<<<p.G, kHistThreads, sm, st>>>(queries, q, p.chunk, p.Ls, p.S, 0, p.S, H, C, map,
                                         (uint32_t)Map::kStageBytes);
-    k_colscan<<<1, 256, 0, st>>>(C, p.G, p.S, CT);
+    colscan_launch(C, p.G, p.S, CT, st);
     k_scan_bins<<<1, 1024, 0, st>>>(CT, p.S, GS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + p.S, 0, (uint32_t)q,
                                     HugeArgs{}, nullptr);
   }
@@ -2164,7 +2198,7 @@ hg_status radix_sort_u64(uint64_t* keys, uint64_t n, uint8_t* ws, cudaStream_t s
     }
     {
       HG_TRACE("k_radix_scan", st);
-      k_colscan<<<1, 256, 0, st>>>(C, G, 256, CT);
+      colscan_launch(C, G, 256, CT, st);
       k_scan_bins<<<1, 1024, 0, st>>>(CT, 256, BS, 0xffffffffu, ovf, &hdr->ovf_count, ovf + 256, 0, (uint32_t)n,
                                       HugeArgs{}, nullptr);
     }
