@@ -246,13 +246,15 @@ struct HugeArgs {
 
 // Exclusive scan of the bin totals (one CTA); list of bins too large for the
 // shared-memory bin build (huge ones split into segments); closing CSR
-// offset offsets[V] = n.
+// offset offsets[V] = n; with wide_count, the number of bins of more than
+// wide_lo and at most emax edges (the bin build's single-buffered launch).
 __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__ T, uint32_t nbins,
                                                     uint32_t* __restrict__ BS, uint32_t emax,
                                                     uint32_t* __restrict__ ovf_list,
                                                     uint32_t* __restrict__ ovf_count,
                                                     uint32_t* __restrict__ offsets, uint64_t V,
-                                                    uint32_t n_end, HugeArgs h, uint32_t* order) {
+                                                    uint32_t n_end, HugeArgs h, uint32_t* order,
+                                                    uint32_t wide_lo = 0, uint32_t* wide_count = nullptr) {
   // Each warp scans a contiguous range of whole 32-bin rows (lane = bin of
   // the row), so every access is coalesced: the range's sum, an exclusive
   // scan of the warp sums, then the range again from its base.
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(1024) k_scan_bins(const uint32_t* __restrict__
     const uint32_t incl = warp_incl_scan(t);
     if (i < nbins) BS[i] = base + incl - t;
     base += __shfl_sync(kFull, incl, 31);
+    if (wide_count && i < nbins && t > wide_lo && t <= emax) atomicAdd(wide_count, 1u);
     if (i >= nbins || t <= emax) continue;
     if (order) *order = 1u;  // this bin is built outside shared memory: stable partitions needed
     if (h.list == nullptr || t <= kHugeSeg) {
@@ -537,6 +540,7 @@ struct BinArgs {
   int nbuf;  // staging buffers: 2 = next bin prefetched during this one
   uint32_t* status;
   const uint32_t* order;  // order mode word (null: partitions were stable); see k_partition
+  const uint32_t* gate;  // null, or a count written by k_scan_bins: the launch returns when it is 0
 };
 
 // Whether the bin build recomputes an edge's bucket rather than keeping it
@@ -651,6 +655,7 @@ size_t bin_smem_bytes(int kb, uint32_t emax, uint32_t s, int nbuf, bool lb) {
 template <typename K, typename Map, int NWB, int MINB, bool LB, bool ANY>
 __global__ void __launch_bounds__(NWB * 32, MINB) k_binbuild(BinArgs<K> a, Map map) {
   if (a.order != nullptr && ((*(volatile const uint32_t*)a.order == 0u) != ANY)) return;
+  if (a.gate != nullptr && *(volatile const uint32_t*)a.gate == 0u) return;  // no bin for this launch
   constexpr uint32_t NBM = kBinBitmapWarps;
   const uint32_t EB = a.emax + 16;
   const int nbuf = a.nbuf;
@@ -1298,6 +1303,8 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
   // Both variants of each such kernel are launched; the one that does not
   // match the order mode returns at once.
   const bool any_order = ids == nullptr || positional_ids;
+  // bins for the single-buffered bin-build launch, counted by k_scan_bins
+  uint32_t* const wide_count = (uint32_t*)&hdr->counters[7];
   {
     HG_TRACE("k_scan_bins", st);
     HugeArgs h{};
@@ -1312,8 +1319,9 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     // bins above the largest the shared-memory bin build takes (the second,
     // single-buffered launch included) go to the oversized-bin kernels
     k_scan_bins<<<1, 1024, 0, st>>>(T, p.nbins, BS, std::max(bc.emax, bc.emax_wide), ovf, &hdr->ovf_count,
-                                    offsets, p.V,
-                                    pos_base + (uint32_t)p.n, h, any_order ? &hdr->order_mode : nullptr);
+                                    offsets, p.V, pos_base + (uint32_t)p.n, h,
+                                    any_order ? &hdr->order_mode : nullptr, bc.emax,
+                                    bc.emax_wide > bc.emax ? wide_count : nullptr);
   }
 
   PartArgs<K> pa{};
@@ -1413,6 +1421,7 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
         bw.emin = bc.emax;
         bw.emax = bc.emax_wide;
         bw.nbuf = 1;
+        bw.gate = wide_count;
         if (any_order) kany<<<grid, threads, bc.smem_wide, st>>>(bw, map);
         kern<<<grid, threads, bc.smem_wide, st>>>(bw, map);
       }
