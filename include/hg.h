@@ -163,7 +163,9 @@ hg_status hg_selftest_wait_timeout(void* d_ws, uint32_t limit_ms, void* stream);
  * HashGraph-Probe-New (Alg. 3, Section 3.4): both inputs are built into
  * tables with the same V and map; bucket v of A is intersected with bucket v
  * of B.  The inner-join size is the number of (a, b) edge pairs with equal
- * keys.
+ * keys.  Both CSRs are walked side by side in bucket order (merge-style); the
+ * bucket map is not evaluated, so the tables must be as hg_build wrote them
+ * (offsets starting at 0, bucket v's edges at [offsets[v], offsets[v+1])).
  * hg_join_count:
  *   d_total          out [1] int64 join size
  *   d_bucket_counts  out [V] int64 pairs per bucket, or NULL
