@@ -339,12 +339,13 @@ hg_status hg_batch_plan_create(int32_t key_type, uint32_t seed, uint32_t num_tab
   for (uint32_t t = 0; t < num_tables; ++t) {
     klen[t] = (uint32_t)P->n[t];
     qlen[t] = (uint32_t)P->q[t];
-    const uint64_t V = P->V[t];
-    const uint64_t M = ~0ull / V + 1;  // Lemire's fastmod constant (0 for V = 1: every hash maps to 0)
+    const uint32_t V = (uint32_t)P->V[t];  // < 2^31
+    uint32_t m = 0, sh1 = 0, sh2 = 0;
+    fastmod_params(V, &m, &sh1, &sh2);    // every V_t, powers of two included
     desc[4 * t + 0] = (uint32_t)P->obeg[t];
-    desc[4 * t + 1] = (uint32_t)V;
-    desc[4 * t + 2] = (uint32_t)M;
-    desc[4 * t + 3] = (uint32_t)(M >> 32);
+    desc[4 * t + 1] = V;
+    desc[4 * t + 2] = m;
+    desc[4 * t + 3] = sh1 | (sh2 << 8);
   }
   auto pages = [&](const std::vector<uint64_t>& beg, uint64_t np, uint32_t* pg) {
     uint32_t t = 0;

@@ -186,15 +186,13 @@ hg_status build_v1(uint64_t n, uint64_t V, const K* keys, const uint32_t* ids, u
 inline MurmurMap make_murmur(uint32_t seed, uint64_t V) {
   MurmurMap m{};
   m.seed = seed;
-  m.mod.d = V;
-  if ((V & (V - 1)) == 0) {
+  if ((V & (V - 1)) == 0) {  // powers of two up to 2^32
     m.mod.pow2 = 1;
     m.mod.mask = (uint32_t)(V - 1);
-    m.mod.M = 0;
-  } else {
+  } else {                   // V < 2^32
     m.mod.pow2 = 0;
-    m.mod.mask = 0;
-    m.mod.M = ~0ull / V + 1;
+    m.mod.d = (uint32_t)V;
+    fastmod_params((uint32_t)V, &m.mod.m, &m.mod.sh1, &m.mod.sh2);
   }
   return m;
 }

@@ -46,19 +46,31 @@ __device__ __forceinline__ uint32_t murmur3(uint64_t key, uint32_t seed) {
   return mm3_finish(h, 8u);
 }
 
-// h mod d for 32-bit h without a divide: Lemire, Kaser and Kurz, "Faster
-// remainder by direct computation" (2019).  M = floor((2^64-1)/d) + 1; then
-// h mod d = high64((M*h mod 2^64) * d).  Powers of two use a mask.
+// h mod d for 32-bit h and 1 <= d < 2^32 without a divide: division by an
+// invariant integer (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994, unsigned case): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, the quotient is
+// (t + ((h - t) >> sh1)) >> sh2 for t = high32(m h), sh1 = min(l, 1),
+// sh2 = max(l - 1, 0).  One 32-bit high multiply and one multiply-subtract.
+// Powers of two (up to 2^32) use a mask.  fastmod_params() sets it up.
 struct FastMod {
-  uint64_t M;
-  uint64_t d;
+  uint32_t d, m, sh1, sh2;
   uint32_t mask;
   uint32_t pow2;
   __device__ __forceinline__ uint32_t operator()(uint32_t h) const {
     if (pow2) return h & mask;
-    return (uint32_t)__umul64hi(M * (uint64_t)h, d);
+    const uint32_t t = __umulhi(m, h);
+    return h - ((t + ((h - t) >> sh1)) >> sh2) * d;
   }
 };
+// Host side: the constants for divisor d (1 <= d < 2^32).
+inline void fastmod_params(uint32_t d, uint32_t* m, uint32_t* sh1, uint32_t* sh2) {
+  uint32_t l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  *m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);  // < 2^32 for every d >= 1
+  *sh1 = l < 1 ? l : 1u;
+  *sh2 = l > 1 ? l - 1 : 0u;
+}
 
 // Bucket maps: operator()(key, pos) gives the bucket of the key at input
 // position pos (plain maps ignore the position; the batched map finds the
@@ -109,7 +121,7 @@ struct BatchedMap {
   const uint64_t* begin;  // [T+1] first position of each table
   const uint32_t* len;    // [T] positions of each table that hold keys
   const uint32_t* page;   // table holding position (p << page_shift)
-  const uint4* desc;      // per table: {global bucket base, V_t, fastmod M low, M high}
+  const uint4* desc;      // per table: {global bucket base, V_t, fastmod m, sh1 | sh2 << 8}
   // The table of the last lookup, kept by each thread: the elements one
   // thread handles mostly belong to the same (large) table, so most lookups
   // become one comparison.  c_lo: the table's first position relative to
@@ -142,8 +154,9 @@ struct BatchedMap {
   __device__ __forceinline__ uint32_t operator()(K key, uint32_t pos) const {
     lookup(pos);
     if (pos - c_lo >= c_len) return c_d.x - bucket_base + c_d.y;
-    const uint64_t M = ((uint64_t)c_d.w << 32) | c_d.z;
-    const uint32_t local = (uint32_t)__umul64hi(M * (uint64_t)murmur3(key, seed), (uint64_t)c_d.y);
+    // murmur3 mod V_t (see FastMod)
+    const uint32_t h = murmur3(key, seed), t = __umulhi(c_d.z, h);
+    const uint32_t local = h - ((t + ((h - t) >> (c_d.w & 255u))) >> (c_d.w >> 8)) * c_d.y;
     return c_d.x - bucket_base + local;
   }
   // ids are stored table-local: position minus the table's first position
