@@ -1391,6 +1391,10 @@ hg_status build_v2(const Plan& p, const K* keys, const uint32_t* ids, uint32_t* 
     if (any_order) launch(k_partition<K, Map, true, kPartIPTB, partb_nw<true>(), partb_minb<true>(), true>, partb_nw<true>());
     launch(k_partition<K, Map, true, kPartIPTB, partb_nw<false>(), partb_minb<false>(), false>, partb_nw<false>());
   }
+  // A partition that could not be launched (say, a tile geometry built in at
+  // compile time that needs more shared memory than a CTA may have) left the
+  // bins unwritten: stop before the bin build reads them.
+  if (cudaPeekAtLastError() != cudaSuccess) return last_launch_status();
   BinArgs<K> ba{};
   ba.in_k = bk;
   ba.in_i = bi;
@@ -1587,6 +1591,7 @@ hg_status build_slabs(const hg_config* cfg, const SlabPlan& p, const K* keys, co
     HG_TRACE("k_partition_slab", st);
     kern<<<p.G, kPartNW * 32, own + pa.stage_bytes, st>>>(pa, map);
   }
+  if (cudaPeekAtLastError() != cudaSuccess) return last_launch_status();  // partition not launched
   // 3. slab sizes to the host, then one two-level build per slab
   uint32_t hT[256];
   if (cudaMemcpyAsync(hT, T, (size_t)p.S * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HG_ERR_CUDA;
@@ -1972,6 +1977,9 @@ hg_status probe_binned_impl(const ProbePlan& p, uint64_t V, const hg_table* t, c
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, sm, st>>>(pa, map);
   }
+  // the probe and the merge index by the grouped positions: none may run on
+  // a query partition that was not launched
+  if (cudaPeekAtLastError() != cudaSuccess) return last_launch_status();
   hg_status rc = probe_launch<K, Map>(qk, q, t->d_offsets, (const K*)t->d_keys, qc, V, st, map,
                                       Map::kNeedsPos ? qi : nullptr);
   if (rc != HG_OK) return rc;
@@ -2093,6 +2101,7 @@ hg_status probe_slabs(const hg_config* cfg, const SlabProbePlan& p, const hg_tab
     HG_TRACE("k_partition_Q", st);
     kern<<<p.G, kPartNW * 32, own + pa.stage_bytes, st>>>(pa, map);
   }
+  if (cudaPeekAtLastError() != cudaSuccess) return last_launch_status();  // partition not launched
   // 2. slab query counts to the host, then the binned probe of every slab
   uint32_t hGS[257];
   if (cudaMemcpyAsync(hGS, GS, ((size_t)p.S + 1) * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return HG_ERR_CUDA;
