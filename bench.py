@@ -166,10 +166,19 @@ def src_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, units: int):
+# The workload the committed DRAM captures were taken on: uint32 keys with
+# implicit ids, Murmur map, V = N (load 1), 50% hits, inputs beyond L2.  Other
+# workloads run other kernel instantiations or other bytes per unit (8-byte
+# keys, another load factor, an L2-resident table), so they get no figure.
+TRAFFIC_WORKLOAD = "scale"
+
+
+def recorded_traffic(kernel: str, units: int, workload: str | None = None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
-    by the units (keys or queries) one launch processes; None when absent or
-    taken on other kernel sources."""
+    by the units (keys or queries) one launch processes; None when absent,
+    taken on other kernel sources, or taken on another workload."""
+    if workload != TRAFFIC_WORKLOAD:
+        return None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
@@ -221,7 +230,8 @@ def algo_join(kb: int, nA: int, nB: int, V: int, M: int) -> dict:
     }
 
 
-def roofline(prof: dict, algo: dict, steps: int, elapsed_ms: float, hbm: float, peak_src: str, units: dict):
+def roofline(prof: dict, algo: dict, steps: int, elapsed_ms: float, hbm: float, peak_src: str, units: dict,
+             workload: str | None = None):
     """Per-kernel rates from the live CUDA-event profile.  algo and units are
     per step (all launches of the kernel in one step); achieved = bytes moved
     over the kernel's total time, i.e. per launch on average."""
@@ -241,7 +251,7 @@ def roofline(prof: dict, algo: dict, steps: int, elapsed_ms: float, hbm: float, 
     ach = algo[dom] * steps / (ms * 1e-3) / 1e9
     per_launch_units = units.get(dom, 0) * steps / max(c, 1)
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(ach / hbm, 4), "traffic": recorded_traffic(dom, per_launch_units),
+            "frac": round(ach / hbm, 4), "traffic": recorded_traffic(dom, per_launch_units, workload),
             "peak_source": f"hbm_gbs of {peak_src}"}
     return roof, phases
 
@@ -466,7 +476,11 @@ def run_scale(c: Ctx):
         for k in ("k_hist", "k_partition_A", "k_partition_B", "k_binbuild"):
             algo.pop(k)
     units = {k: (q if k in PROBE_KERNELS else n) for k in algo}
-    roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units)
+    # the committed DRAM captures hold for this shape only (sizes they were taken at)
+    captured_shape = (args.log2n in (27, 28) and V == n and args.hit == 0.5 and args.dup == 0
+                      and not args.explicit_ids and args.algo == "v2" and binned)
+    roof, phases = roofline(prof, algo, args.steps, elapsed_ms, c.hbm, c.peak_src, units,
+                            TRAFFIC_WORKLOAD if captured_shape else None)
     build_ms = sum(prof[k][0] for k in prof if k not in PROBE_KERNELS) / args.steps
     probe_ms = sum(prof[k][0] for k in prof if k in PROBE_KERNELS) / args.steps
 

@@ -39,11 +39,11 @@ def test_direct_probe_counts_sectors(bench):
 
 
 def test_roofline_picks_the_longest_kernel(bench, monkeypatch):
-    monkeypatch.setattr(bench, "recorded_traffic", lambda k, u: ("traffic", k, u))
+    monkeypatch.setattr(bench, "recorded_traffic", lambda k, u, w=None: ("traffic", k, u))
     algo = {"k_a": 1_000_000_000, "k_b": 4_000_000_000}
     prof = {"k_a": (2.0, 4), "k_b": (10.0, 2), "k_untracked": (50.0, 1)}
     roof, phases = bench.roofline(prof, algo, steps=2, elapsed_ms=100.0, hbm=1000.0, peak_src="measured",
-                                  units={"k_a": 10, "k_b": 100})
+                                  units={"k_a": 10, "k_b": 100}, workload=bench.TRAFFIC_WORKLOAD)
     assert roof["kernel"] == "k_b"                                       # the untracked kernel is not a candidate
     assert roof["achieved"] == pytest.approx(4e9 * 2 / 10e-3 / 1e9)      # 800 GB/s
     assert roof["frac"] == pytest.approx(0.8)
@@ -61,10 +61,13 @@ def test_recorded_traffic_follows_the_source_digest(bench, monkeypatch, tmp_path
     dig = bench.src_digest()
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
         {"k_probe": {"bytes_per_unit": 23.5, "units": "queries", "src_digest": dig}}))
-    assert bench.recorded_traffic("k_probe", 1000) == 23500
-    assert bench.recorded_traffic("k_other", 1000) is None
+    w = bench.TRAFFIC_WORKLOAD
+    assert bench.recorded_traffic("k_probe", 1000, w) == 23500
+    assert bench.recorded_traffic("k_other", 1000, w) is None
+    assert bench.recorded_traffic("k_probe", 1000) is None              # another workload: no figure
+    assert bench.recorded_traffic("k_probe", 1000, "join") is None
     (csrc / "k.cu").write_text("// v2\n")                               # the kernel changed since the capture
-    assert bench.recorded_traffic("k_probe", 1000) is None
+    assert bench.recorded_traffic("k_probe", 1000, w) is None
 
 
 def test_committed_traffic_record_is_well_formed(bench):
