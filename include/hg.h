@@ -15,7 +15,9 @@
  *     CUDA caching allocator are); other device arrays to their element size.
  *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
  *     default stream).  Argument errors are returned synchronously and launch
- *     nothing.  A failed launch returns HG_ERR_CUDA.
+ *     nothing.  A failed launch returns HG_ERR_CUDA; a build or binned probe
+ *     whose partition launch failed returns before any kernel that would read
+ *     the partition's output is launched.
  *   - Calls that take a workspace write a device status word into it (bounded
  *     waits that gave up, capacity overflow).  Read it after the stream has
  *     finished with hg_workspace_status().
