@@ -72,7 +72,7 @@ static hg_status choose_algo(const hg_config* cfg, uint64_t n, BuildKind* kind, 
   return HG_OK;
 }
 
-static size_t build_ws_bytes(const hg_config* cfg, uint64_t n, BuildKind kind, const Plan& p, const SlabPlan& sp) {
+static size_t build_ws_bytes_of(const hg_config* cfg, uint64_t n, BuildKind kind, const Plan& p, const SlabPlan& sp) {
   if (kind == kBuildV2) return p.total;
   if (kind == kBuildSlabs) return sp.total;
   return v1_workspace_bytes(cfg->key_type == HG_KEY_U64 ? 8 : 4, n, cfg->num_buckets);
@@ -106,7 +106,7 @@ size_t hg_build_workspace_size(const hg_config* cfg, uint64_t n) {
   Plan p{};
   SlabPlan sp{};
   if (choose_algo(cfg, n, &kind, &p, &sp) != HG_OK) return 0;
-  return build_ws_bytes(cfg, n, kind, p, sp);
+  return build_ws_bytes_of(cfg, n, kind, p, sp);
 }
 
 hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_ids, uint64_t n,
@@ -125,7 +125,7 @@ hg_status hg_build(const hg_config* cfg, const void* d_keys, const uint32_t* d_i
   SlabPlan sp{};
   rc = choose_algo(cfg, n, &kind, &p, &sp);
   if (rc != HG_OK) return rc;
-  if (ws_bytes < build_ws_bytes(cfg, n, kind, p, sp)) return HG_ERR_WORKSPACE_TOO_SMALL;
+  if (ws_bytes < build_ws_bytes_of(cfg, n, kind, p, sp)) return HG_ERR_WORKSPACE_TOO_SMALL;
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_ws, 0, sizeof(WsHeader), st) != cudaSuccess) return HG_ERR_CUDA;
   if (n == 0) {
@@ -236,6 +236,29 @@ hg_status hg_build_probe_host(const hg_config* cfg, const void* h_keys, uint64_t
   if (!table || table->n != n || (n > 0 && (!h_keys || !d_keys)) || (q > 0 && (!h_queries || !h_counts)))
     return HG_ERR_INVALID_ARG;
   const size_t kb = cfg->key_type == HG_KEY_U64 ? 8 : 4;
+  // Everything the build and the probe below would refuse is refused here,
+  // before the first copy is enqueued, so an argument error launches nothing.
+  if (n >= (1ull << 32) || (d_probe_ws && q >= (1ull << 32))) return HG_ERR_INVALID_ARG;
+  if (!table->d_offsets || !d_build_ws || (n > 0 && (!table->d_keys || !table->d_ids)) ||
+      (q > 0 && (!d_queries || !d_counts)))
+    return HG_ERR_INVALID_ARG;
+  if (!aligned(d_keys, 16) || !aligned(table->d_keys, 16) || !aligned(table->d_ids, 16) ||
+      !aligned(table->d_offsets, 4) || !aligned(d_queries, d_probe_ws ? 16 : kb) || !aligned(d_counts, 4) ||
+      !aligned(d_build_ws, 256) || !aligned(d_probe_ws, 256))
+    return HG_ERR_INVALID_ARG;
+  {
+    BuildKind kind = kBuildV1;
+    Plan p{};
+    SlabPlan sp{};
+    rc = choose_algo(cfg, n, &kind, &p, &sp);
+    if (rc != HG_OK) return rc;
+    if (build_ws_bytes < build_ws_bytes_of(cfg, n, kind, p, sp)) return HG_ERR_WORKSPACE_TOO_SMALL;
+  }
+  if (q > 0 && d_probe_ws) {
+    const size_t need = hg_probe_workspace_size(cfg, n, q);
+    if (need == 0) return HG_ERR_UNSUPPORTED;
+    if (probe_ws_bytes < need) return HG_ERR_WORKSPACE_TOO_SMALL;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   // one call at a time per device enqueues, so that the device sees the
   // calls in one order

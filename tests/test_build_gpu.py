@@ -235,6 +235,44 @@ def test_build_probe_host_buffers(hg, orc, pinned, binned):
     assert np.array_equal(off, roff) and np.array_equal(ck, rk) and np.array_equal(ci, ri)
 
 
+def test_build_probe_host_refuses_before_copying(hg):
+    """The host-buffer call finds argument errors before it enqueues the first
+    copy: a probe workspace one byte short, a staging buffer for the queries
+    that is missing, or a build workspace one byte short each raise, and the
+    device staging buffer for the keys keeps the contents it had."""
+    import torch
+    n, V = (1 << 12) + 5, 1 << 12
+    keys = dg.uniform_keys_u32(n, 71)
+    q = dg.queries_u32(n, keys, 0.5, 72)
+    hk = torch.from_numpy(keys.view(np.int32).copy()).pin_memory()
+    hq = torch.from_numpy(q.view(np.int32).copy()).pin_memory()
+    hc = torch.zeros(len(q), dtype=torch.int32).pin_memory()
+    cfg = hg.make_config(hg.KEY_U32, V, 0, "v2")
+    dev = "cuda"
+    t = hg.Table(torch.empty(V + 1, dtype=torch.uint32, device=dev), torch.empty(n, dtype=torch.uint32, device=dev),
+                 torch.empty(n, dtype=torch.uint32, device=dev), cfg)
+    ws = torch.empty(hg.build_workspace_size(cfg, n), dtype=torch.uint8, device=dev)
+    pws = torch.empty(hg.probe_workspace_size(t, len(q)), dtype=torch.uint8, device=dev)
+    dk = torch.full((n,), 0x5A5A5A5A, dtype=torch.int32, device=dev).view(torch.uint32)
+    dq = torch.empty(len(q), dtype=torch.uint32, device=dev)
+    dc = torch.empty(len(q), dtype=torch.uint32, device=dev)
+    for bad in ("probe_ws", "d_queries", "build_ws"):
+        args = dict(d_queries=dq, ws=ws, probe_ws=pws)
+        if bad == "probe_ws":
+            args["probe_ws"] = pws[:-1]
+        elif bad == "build_ws":
+            args["ws"] = ws[:-1]
+        else:
+            args["d_queries"] = torch.empty(0, dtype=torch.uint32, device=dev)  # a null staging pointer
+        with pytest.raises(hg.HGError):
+            hg.build_probe_host(cfg, hk, hq, hc, dk, args["d_queries"], dc, t, args["ws"], args["probe_ws"])
+        torch.cuda.synchronize()
+        assert bool((dk.view(torch.int32) == 0x5A5A5A5A).all()), bad
+    hg.build_probe_host(cfg, hk, hq, hc, dk, dq, dc, t, ws, pws)  # the same call with valid arguments
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(dk), keys)
+
+
 def test_build_probe_host_batches_in_flight(hg, orc):
     """Several host-buffer calls on two streams that reuse two sets of device
     staging buffers: every call's counts and last table equal the oracle's
