@@ -79,6 +79,34 @@ def test_argument_errors_return_synchronously(libs):
     assert lib.hg_join_count(ctypes.byref(cfg), None, None, fake, None, fake, 1 << 20, None) == 1
 
 
+def test_host_buffer_call_refuses_before_any_device_work(libs):
+    """hg_build_probe_host checks everything the build and the probe would
+    refuse before it enqueues its first copy; on a machine without a GPU the
+    refusals therefore still come back as argument errors, not CUDA errors."""
+    import paper_1907_02900_gb300 as hg
+    lib = hg.load()
+    n, q, V = 1000, 500, 1 << 10
+    cfg = hg.make_config(hg.KEY_U32, V, 0, "v2")
+    fake, mis = ctypes.c_void_p(0x10000), ctypes.c_void_p(0x10004)
+    host = ctypes.c_void_p(0x20000)
+    tv = hg.hg_table(n, 0x30000, 0x40000, 0x50000)
+    ws_need = hg.build_workspace_size(cfg, n)
+    pws_need = int(lib.hg_probe_workspace_size(ctypes.byref(cfg), n, q))
+    assert ws_need > 0 and pws_need > 0
+
+    def call(table=tv, d_keys=fake, d_queries=fake, ws_bytes=ws_need, pws_bytes=pws_need, d_pws=fake):
+        return lib.hg_build_probe_host(ctypes.byref(cfg), host, n, host, q, host, d_keys, d_queries, fake,
+                                       ctypes.byref(table), fake, ws_bytes, d_pws, pws_bytes, None)
+
+    assert call(table=hg.hg_table(n + 1, 0x30000, 0x40000, 0x50000)) == 1   # table size differs from n
+    assert call(table=hg.hg_table(n, 0x30000, 0x40004, 0x50000)) == 1       # table keys misaligned
+    assert call(d_keys=mis) == 1                                            # key staging misaligned
+    assert call(d_queries=ctypes.c_void_p(0)) == 1                          # no query staging buffer
+    assert call(ws_bytes=ws_need - 1) == 2                                  # build workspace short
+    assert call(pws_bytes=pws_need - 1) == 2                                # probe workspace short
+    assert call(d_pws=mis) == 1                                             # probe workspace misaligned
+
+
 def test_workspace_sizes_cover_intermediate_arrays(libs):
     import paper_1907_02900_gb300 as hg
     for kt, kb in ((hg.KEY_U32, 4), (hg.KEY_U64, 8)):
