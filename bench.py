@@ -166,6 +166,10 @@ def src_digest() -> str:
     return h.hexdigest()[:16]
 
 
+# Nominal HBM3e bandwidth of a GB300 (about 8 TB/s), reported beside the
+# measured copy bandwidth, which is the roofline's peak.
+HBM_NOMINAL_GBS = 8000.0
+
 # The workload the committed DRAM captures were taken on: uint32 keys with
 # implicit ids, Murmur map, V = N (load 1), 50% hits, inputs beyond L2.  Other
 # workloads run other kernel instantiations or other bytes per unit (8-byte
@@ -252,7 +256,8 @@ def roofline(prof: dict, algo: dict, steps: int, elapsed_ms: float, hbm: float, 
     per_launch_units = units.get(dom, 0) * steps / max(c, 1)
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(ach / hbm, 4), "traffic": recorded_traffic(dom, per_launch_units, workload),
-            "peak_source": f"hbm_gbs of {peak_src}"}
+            "peak_source": f"hbm_gbs of {peak_src}",
+            "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": round(ach / HBM_NOMINAL_GBS, 4)}
     return roof, phases
 
 

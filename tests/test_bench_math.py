@@ -47,6 +47,7 @@ def test_roofline_picks_the_longest_kernel(bench, monkeypatch):
     assert roof["kernel"] == "k_b"                                       # the untracked kernel is not a candidate
     assert roof["achieved"] == pytest.approx(4e9 * 2 / 10e-3 / 1e9)      # 800 GB/s
     assert roof["frac"] == pytest.approx(0.8)
+    assert roof["peak_nominal"] == 8000.0 and roof["frac_nominal"] == pytest.approx(0.1)  # 800 of 8000 GB/s
     assert roof["traffic"] == ("traffic", "k_b", 100.0)                  # units per launch: 100 * 2 steps / 2
     assert phases["k_a"]["avg_ms"] == 0.5 and phases["k_a"]["algo_bytes_per_launch"] == 500_000_000
     assert phases["k_untracked"]["share"] == 0.5 and "frac" not in phases["k_untracked"]
