@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <unordered_map>
 
 #include "hg_build.cuh"
 #include "hg_trace.h"
@@ -1254,10 +1255,23 @@ __global__ void k_v1_ids(uint32_t* __restrict__ csr_i, const uint32_t* __restric
 // ===========================================================================
 // Host drivers
 // ===========================================================================
+// The largest dynamic shared memory each kernel was asked for, per device.
+static std::mutex g_smem_mu;
+static std::unordered_map<const void*, size_t> g_smem_max[64];
+
 template <typename F>
 static void set_smem_once(F* kernel, size_t bytes) {
-  // The attribute is per kernel; setting it every call is cheap and idempotent.
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  // The attribute belongs to the kernel, process-wide, and a launch needs it
+  // at least as large as its own request.  It is raised to the largest
+  // request so far and never lowered, so a call on another host thread that
+  // asked for more is not cut short; it is set on every call (cheap), so it
+  // holds again after a device reset.
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& top = g_smem_max[dev][(const void*)kernel];
+  if (bytes > top) top = bytes;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)top);
 }
 
 template <typename K, typename Map>
