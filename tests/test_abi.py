@@ -77,6 +77,37 @@ def test_argument_errors_return_synchronously(libs):
     # probe with a null table, join with a null table
     assert lib.hg_probe(ctypes.byref(cfg), None, fake, 10, fake, None) == 1
     assert lib.hg_join_count(ctypes.byref(cfg), None, None, fake, None, fake, 1 << 20, None) == 1
+    tv = hg.hg_table(10, 0x30000, 0x40000, 0x50000)
+    # binned probe: null workspace, q >= 2^32, misaligned queries
+    assert lib.hg_probe_binned(ctypes.byref(cfg), ctypes.byref(tv), fake, 10, fake, None, 1 << 30, None) == 1
+    assert lib.hg_probe_binned(ctypes.byref(cfg), ctypes.byref(tv), fake, 1 << 32, fake, fake, 1 << 30, None) == 1
+    assert lib.hg_probe_binned(ctypes.byref(cfg), ctypes.byref(tv), mis, 10, fake, fake, 1 << 30, None) == 1
+    # materialisation: pairs requested without output arrays; the count's follow-up likewise
+    assert lib.hg_join_materialize(ctypes.byref(cfg), ctypes.byref(tv), ctypes.byref(tv), None, None, 5, fake,
+                                   fake, 1 << 30, None) == 1
+    assert lib.hg_join_materialize_after_count(ctypes.byref(cfg), ctypes.byref(tv), ctypes.byref(tv), None, None,
+                                               5, fake, fake, 1 << 30, None) == 1
+    # the no-allocation build: V1 is not offered, n >= 2^32 is refused, and a
+    # plan larger than the fixed array asks for a workspace it cannot have
+    v1 = hg.make_config(hg.KEY_U32, 1 << 10, algo="v1")
+    assert lib.hg_build_static_scratch(ctypes.byref(v1), fake, None, 10, fake, fake, fake, None) == 7
+    assert lib.hg_build_static_scratch(ctypes.byref(cfg), fake, None, 1 << 32, fake, fake, fake, None) == 1
+    big = hg.make_config(hg.KEY_U32, 1 << 28)
+    assert lib.hg_build_static_scratch(ctypes.byref(big), fake, None, 1 << 28, fake, fake, fake, None) == 2
+    # learned map: training without keys or model, a bad key type, statistics without outputs
+    assert lib.hg_learned_train(0, None, 10, 16, 4, 8, 1, 1, fake, None, fake, 1 << 30, None) == 1
+    assert lib.hg_learned_train(3, fake, 10, 16, 4, 8, 1, 1, fake, None, fake, 1 << 30, None) == 1
+    assert lib.hg_learned_train(1, fake, 0, 16, 4, 8, 1, 1, fake, None, fake, 1 << 30, None) == 1
+    assert lib.hg_bucket_stats(ctypes.byref(cfg), fake, 10, None, fake, fake, 1 << 20, None) == 1
+    assert lib.hg_learned_judge(ctypes.byref(cfg), fake, 10, 0.0, 0.0, fake, fake, 1 << 20, None, None, None) == 1
+    # batched plans: no tables, 8-byte keys, a zero bucket count
+    plan = ctypes.c_void_p()
+    sizes = (ctypes.c_uint64 * 2)(100, 200)
+    assert lib.hg_batch_plan_create(hg.KEY_U32, 0, 0, sizes, sizes, None, ctypes.byref(plan)) == 1
+    assert lib.hg_batch_plan_create(hg.KEY_U64, 0, 2, sizes, sizes, None, ctypes.byref(plan)) == 7
+    zero_v = (ctypes.c_uint64 * 2)(100, 0)
+    assert lib.hg_batch_plan_create(hg.KEY_U32, 0, 2, sizes, sizes, zero_v, ctypes.byref(plan)) == 1
+    assert not plan.value
 
 
 def test_host_buffer_call_refuses_before_any_device_work(libs):
