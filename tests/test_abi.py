@@ -146,3 +146,18 @@ def test_workspace_sizes_cover_intermediate_arrays(libs):
             assert sz >= n * (kb + 4), (kt, n, V)
         v1 = hg.build_workspace_size(hg.make_config(kt, 1 << 20, algo="v1"), 1 << 20)
         assert v1 >= (1 << 20) * 4
+
+
+def test_probe_workspace_grows_with_the_query_count(libs):
+    """The slab-grouped probe sizes every slab's binned probe by the plan of
+    all queries, so a plan for fewer queries must never need more workspace."""
+    import paper_1907_02900_gb300 as hg
+    lib = hg.load()
+    for kt in (hg.KEY_U32, hg.KEY_U64):
+        for V in (1, 1000, 1 << 20, 1 << 28):
+            cfg = hg.make_config(kt, V)
+            prev = 0
+            for q in (1, 5, 4095, 4096, 4097, 100_000, 1 << 20, (1 << 20) + 3, 1 << 24):
+                sz = int(lib.hg_probe_workspace_size(ctypes.byref(cfg), 1 << 20, q))
+                assert sz >= prev and sz > 0, (kt, V, q)
+                prev = sz
