@@ -109,6 +109,31 @@ def test_build_zipf_u64(hg, orc):
         _check_build(hg, orc, keys, 1 << 20, algo=algo)
 
 
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("algo", ["v2", "v1"])
+@pytest.mark.parametrize("V", [1, 7, 4096])
+def test_zero_and_largest_key_are_ordinary_keys(hg, orc, kt, algo, V):
+    """No key value is reserved (the table is a CSR, not open addressing):
+    key 0 and the largest key of the width are built, probed and counted like
+    any other, next to random keys."""
+    rng = np.random.default_rng(91)
+    dt = np.uint32 if kt == "u32" else np.uint64
+    top = np.iinfo(dt).max
+    n = 5003
+    keys = (dg.uniform_keys_u32(n, 92) if kt == "u32" else dg.uniform_keys_u64(n, 92)).copy()
+    keys[rng.integers(0, n, 40)] = 0
+    keys[rng.integers(0, n, 25)] = top
+    keys[:3] = [0, top, 0]
+    _check_build(hg, orc, keys, V, seed=4, algo=algo)
+    q = np.concatenate([np.array([0, top, 1, top - 1], dtype=dt), keys[rng.integers(0, n, 3000)],
+                        (dg.uniform_keys_u32(3000, 93) if kt == "u32" else dg.uniform_keys_u64(3000, 93))])
+    t = hg.build(to_dev(keys), V, seed=4, algo=algo)
+    want = orc.multiplicity(keys, q)
+    assert want[0] == int((keys == 0).sum()) and want[1] == int((keys == top).sum())
+    assert np.array_equal(to_np(hg.probe(t, to_dev(q), binned=False)), want)
+    assert np.array_equal(to_np(hg.probe(t, to_dev(q), binned=True)), want)
+
+
 def test_build_sequence_input(hg, orc):
     _check_build(hg, orc, dg.sequence_keys_u32(1 << 21), 1 << 20)
 
