@@ -27,6 +27,31 @@ def test_join_count_u32(hg, orc, V):
     assert np.array_equal(to_np(per), rper)
 
 
+@pytest.mark.parametrize("kt", ["u32", "u64"])
+@pytest.mark.parametrize("V", [1, 7, 4096])
+def test_join_with_zero_and_largest_keys(hg, orc, kt, V):
+    """Key 0 and the largest key of the width join like any other key: both
+    sides hold several copies of each, next to random keys of a small domain."""
+    rng = np.random.default_rng(101)
+    dt = np.uint32 if kt == "u32" else np.uint64
+    top = np.iinfo(dt).max
+    dom = rng.integers(1, 1 << 30, 300).astype(dt)
+    a = dom[rng.integers(0, 300, 4000)]
+    b = dom[rng.integers(0, 300, 3000)]
+    a[rng.integers(0, 4000, 30)] = 0
+    a[rng.integers(0, 4000, 20)] = top
+    b[rng.integers(0, 3000, 10)] = 0
+    b[rng.integers(0, 3000, 15)] = top
+    tA, tB, rA, rB = _tables(hg, orc, a, b, V, seed=6)
+    total, per = hg.join_count(tA, tB)
+    rt, rper = orc.join_count(rA[0], rA[1], rB[0], rB[1], V)
+    assert int(total.item()) == rt == orc.join_size_by_keys(a, b)
+    assert np.array_equal(to_np(per), rper)
+    pa, pb = hg.join_materialize(tA, tB)
+    ra, rb = orc.join_materialize(rA[0], rA[1], rA[2], rB[0], rB[1], rB[2], V)
+    assert np.array_equal(to_np(pa), ra) and np.array_equal(to_np(pb), rb)
+
+
 def test_join_count_zipf_u64(hg, orc):
     # Section 5 join workload shape: Zipf(1) build side vs uniform probe side.
     a = dg.zipf_keys_u64(1 << 20, 1 << 17, 3)
