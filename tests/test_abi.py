@@ -161,3 +161,35 @@ def test_probe_workspace_grows_with_the_query_count(libs):
                 sz = int(lib.hg_probe_workspace_size(ctypes.byref(cfg), 1 << 20, q))
                 assert sz >= prev and sz > 0, (kt, V, q)
                 prev = sz
+
+
+def test_header_is_plain_c_and_links(libs, tmp_path):
+    """include/hg.h is a C header: a C99 program that takes the address of
+    every declared entry point compiles without warnings (-Wall -Wextra
+    -pedantic -Werror) and links against libhg.so."""
+    import shutil
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not available")
+    header = os.path.join(ROOT, "include", "hg.h")
+    names = _declared(header)
+    src = tmp_path / "uses_every_entry_point.c"
+    body = "\n".join(f"  fns[{i}] = (void (*)(void))&{n};" for i, n in enumerate(names))
+    src.write_text(f"""#include <stdio.h>
+#include "hg.h"
+int main(void) {{
+  void (*fns[{len(names)}])(void);
+{body}
+  for (unsigned i = 0; i < {len(names)}; ++i)
+    if (!fns[i]) return 1;
+  puts(hg_version());
+  return 0;
+}}
+""")
+    exe = str(tmp_path / "uses_every_entry_point")
+    lib = libs["libhg.so"]
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(header),
+                        str(src), "-o", exe, lib, "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert run.returncode == 0 and "sm_103a" in run.stdout, run.stdout + run.stderr
